@@ -1,0 +1,309 @@
+"""Throughput of the staggered-grid P_N step on GB300, one JSON line on stdout.
+
+Workload (default): P39 (1600 moments) on 200^3 periodic cells, FP32 storage and arithmetic,
+sigma_s log-uniform in [0.1, 10] per 8^3 block, sigma_a = 0.01, q = 0, Gaussian u_0 (width 0.1 of
+the unit box, unit sum).  A bench "step" is one full time step of Eq. (6) (the merged schedule:
+one even and one odd pass per step).  The 51 GB state is far larger than L2, so no flush is needed
+between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica (independent instances, no
+collective); value = all ranks' updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "P_N moment-cell updates/s, % HBM peak; FP32/BF16 vs FP64 at stated error"
+UNIT = "MLCUP/s"  # million lattice cell component updates (moment-cell updates) per second
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--N", type=int, default=39)
+    p.add_argument("--n", type=int, default=200)
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    p.add_argument("--kernel", default="auto", choices=["auto", "generic", "window"])
+    p.add_argument("--tile", default="0,0,0")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(args):
+    return {"workload": f"P{args.N} {args.n}^3 periodic random-block media, Gaussian u_0",
+            "N": args.N, "cells": args.n ** 3, "moments": (args.N + 1) ** 2,
+            "storage": args.precision, "kernel": args.kernel,
+            "l2_flush": "not needed: state larger than L2 (inputs larger than L2)"}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={device_index}",
+                                       f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(args, steps: int):
+    """The FP64 oracle, as it stands, on a bounded sample: the same rules at 24^3 (same per-cell work)."""
+    from oracle import stepper as st
+    from paper_2004_02833_gb300 import synth
+
+    n = 24
+    inst = synth.random_blocks(args.N, n, seed=2)
+    P = st.Problem(inst.N, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, inst.bc)
+    u = inst.full_state()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u = P.step(u)
+    dt = time.perf_counter() - t0
+    mcu = inst.n_c * n ** 3 * steps
+    return {"value": mcu / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"P{args.N} {n}^3 periodic random-block instance, {steps} steps "
+                      f"(serial numpy FP64, {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle timed on host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from oracle import stepper as st
+    from paper_2004_02833_gb300 import synth
+
+    n = 24
+    inst = synth.random_blocks(args.N, n, seed=2)
+    P = st.Problem(inst.N, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, inst.bc)
+    u = inst.full_state()
+    for _ in range(args.warmup):
+        u = P.step(u)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = P.step(u)
+    dt = time.perf_counter() - t0
+    mcu = inst.n_c * n ** 3 * args.steps
+    value = mcu / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"P{args.N} {n}^3 periodic random-block instance per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    from paper_2004_02833_gb300 import rtpn, synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    inst = synth.random_blocks(args.N, args.n, seed=2 + rank)
+    tile = tuple(int(x) for x in args.tile.split(","))
+    stream = torch.cuda.Stream()
+    ctx = rtpn.Context(args.N, inst.shape, inst.h, inst.bc, args.precision, inst.dt)
+    ctx.set_stream(stream)
+    if args.kernel != "auto" or any(tile):
+        ctx.set_kernel(args.kernel, tile)
+    info = ctx.info()
+    with torch.cuda.stream(stream):
+        media = [torch.tensor(a, dtype=torch.float32, device="cuda")
+                 for a in (inst.sigma_a, inst.sigma_s, inst.q)]
+        u0 = torch.tensor(inst.u0, dtype=torch.float32, device="cuda")
+    ctx.zero_moments()
+    ctx.set_media(*media)
+    ctx.set_component(0, u0)
+    ctx.step(args.warmup)
+    ctx.synchronize()
+
+    # ---- timed region: K full steps, inputs resident in HBM
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ctx.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    mcu_step = inst.n_c * inst.shape[0] * inst.shape[1] * inst.shape[2]
+    value = world * mcu_step * args.steps / (ms / 1e3) / 1e6
+    nonfinite = ctx.count_nonfinite()
+
+    # ---- per-launch duration of the dominant kernel (the even and the odd substep pass)
+    per_pass = pass_durations(ctx, stream, reps=max(3, min(10, args.steps)))
+    s = {"fp32": 4, "bf16": 2, "fp64": 8}[args.precision]
+    V = inst.shape[0] * inst.shape[1] * inst.shape[2]
+    # algorithmic bytes of one pass: every moment read once, the pass's class written once,
+    # plus the media share (12 B per cell per step, i.e. 6 B per pass)
+    alg = {cls: V * ((info.n_c + n_a) * s + 6) for cls, n_a in ((0, info.n_even), (1, info.n_odd))}
+    dom = max(per_pass, key=lambda c: per_pass[c])
+    hbm, peak_kind = peaks()
+    achieved = alg[dom] / (per_pass[dom] / 1e3) / 1e9
+    step_ms = ms / args.steps
+    step_bytes = V * (info.n_c * 2 * s + 12)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None,
+                "kernel": f"substep pass ({'even' if dom == 0 else 'odd'} class)",
+                "peak_kind": peak_kind,
+                "pass_ms": {"even": per_pass[0], "odd": per_pass[1]},
+                "step_alg_bytes_per_mcu": step_bytes / mcu_step,
+                "step_frac": step_bytes / (step_ms / 1e3) / 1e9 / hbm}
+
+    # ---- end to end through the C ABI with host buffers (inputs u_0 and media; output u_0)
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(ctx, inst, args, mcu_step, world, dist)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, steps=5)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16",
+                                                                "fp64": "f64"}[args.precision],
+            "data": "synthetic", "config": workload_config(args),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": 2 * args.steps + 1, "nonfinite": nonfinite,
+            "kernel_used": {1: "generic", 2: "window"}.get(ctx.info().kernel, "?")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def pass_durations(ctx, stream, reps: int):
+    """Average duration (ms) of the even and the odd pass, each timed alone with CUDA events on the
+    launching stream (one merged-schedule step = even pass + odd pass)."""
+    import torch
+
+    out = {}
+    for cls in (0, 1):
+        evs = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx._pass(cls)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        out[cls] = sum(a.elapsed_time(b) for a, b in evs) / reps
+    return out
+
+
+def end_to_end(ctx, inst, args, mcu_step, world, dist):
+    """One user job through the C ABI with pinned host buffers: upload media and u_0, zero the
+    other moments, advance K steps, read u_0 back.  Copies are inside the timed region."""
+    import torch
+
+    host = [torch.tensor(a, dtype=torch.float32).pin_memory()
+            for a in (inst.sigma_a, inst.sigma_s, inst.q, inst.u0)]
+    out = torch.empty(inst.shape, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    ctx.set_media(host[0], host[1], host[2])
+    ctx.zero_moments()
+    ctx.set_component(0, host[3])
+    ctx.step(args.steps)
+    ctx.get_component(0, out)
+    ctx.synchronize()
+    dt = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    h2d = sum(h.numel() * 4 for h in host)
+    d2h = out.numel() * 4
+    return {"value": world * mcu_step * args.steps / dt / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+            "job": f"set_media + zero + set u_0 from pinned host, {args.steps} steps, u_0 to host"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * rtpn.h -- C ABI of the GB300 staggered-grid P_N time step.
+ *
+ * The library advances the real 3D P_N moment system of Eq. (3) of Berghoff, Frank & Seibold,
+ * "Massively Parallel Stencil Strategies for Radiation Transport Moment Model Simulations"
+ * (arXiv 2004.02833):
+ *
+ *     du/dt + Mx du/dx + My du/dy + Mz du/dz + C u = q ,
+ *
+ * on a box of nx * ny * nz cells with the StaRMAP staggered-grid method of Section 2.1: the
+ * (N+1)^2 moments live on 8 staggered sub-grids, x/y/z derivatives are two-point half-grid
+ * differences, each class ("even"/"odd" grids) is advanced with the dual class frozen by the exact
+ * scalar solution of Eq. (5), and one step is the Strang splitting of Eq. (6).
+ *
+ * Conventions used by every entry point:
+ *   - A component index c at this interface is c = l*l + l + m (l = 0..N, m = -l..l).  The real
+ *     basis has no Condon-Shortley phase: m > 0 is sqrt(2) N_l^m P_l^m(mu) cos(m phi), m < 0 the
+ *     matching sin(|m| phi), m = 0 is N_l^0 P_l(mu), polar axis z.
+ *   - Per-cell arrays are [z][y][x] with x fastest (nx*ny*nz values).  A full state is
+ *     [c][z][y][x] ((N+1)^2 * nx*ny*nz values).  A component with sub-grid slot g = 1 along an axis
+ *     sits at (i + 1/2) h on that axis, g = 2 at (i + 1) h (0-based cell i).
+ *   - `where` says whether a caller pointer is host (RTPN_HOST) or device (RTPN_DEVICE) memory.
+ *     Caller buffers are never retained.  Calls with host pointers synchronise before returning;
+ *     calls with device pointers are ordered on the context stream and return without waiting.
+ *   - Every call returns RTPN_OK (0) or a negative RTPN_E* code; rtpn_last_error() gives the
+ *     context's last message.  A failed call leaves the state as it was unless stated otherwise.
+ *   - The library owns all device memory it allocates; nothing here takes torch types.
+ */
+#ifndef RTPN_H
+#define RTPN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define RTPN_OK            0
+#define RTPN_EINVAL       -1   /* bad argument (N < 0, dims < 1, h <= 0, bad enum, NULL, ...)     */
+#define RTPN_ECFL         -2   /* dt >= min(h)/3: outside the proven range of Section 2.1         */
+#define RTPN_ENOMEM       -3   /* device allocation failed                                        */
+#define RTPN_ECUDA        -4   /* a CUDA call failed (message in rtpn_last_error)                 */
+#define RTPN_ETIMEOUT     -5   /* a bounded device wait ran out                                   */
+#define RTPN_ENONFINITE   -6   /* NaN or Inf found by a diagnostic                                */
+#define RTPN_EUNSUPPORTED -7   /* valid request this build does not implement                     */
+#define RTPN_ESTATE       -8   /* call out of order (e.g. rtpn_step before rtpn_set_media)        */
+
+/* ---- boundaries ---- */
+#define RTPN_BC_PERIODIC 0     /* Section 2.1: indices wrap                                       */
+#define RTPN_BC_VACUUM   1     /* every out-of-domain value of every component reads as 0        */
+
+/* ---- storage precision of the state (arithmetic is FP32 for FP32/BF16, FP64 for FP64) ---- */
+#define RTPN_FP64 0
+#define RTPN_FP32 1
+#define RTPN_BF16 2
+
+/* ---- data types of caller arrays ---- */
+#define RTPN_DTYPE_F64 0
+#define RTPN_DTYPE_F32 1
+
+/* ---- memory kinds of caller pointers ---- */
+#define RTPN_HOST   0
+#define RTPN_DEVICE 1
+
+/* ---- step kernels ---- */
+#define RTPN_KERNEL_AUTO    0  /* fastest available for (N, precision)                            */
+#define RTPN_KERNEL_GENERIC 1  /* any N and precision: one thread per cell, partner-table gather   */
+#define RTPN_KERNEL_WINDOW  2  /* FP32/BF16, compiled N: register-window scatter over m-columns  */
+
+typedef struct rtpn_ctx rtpn_ctx;
+
+typedef struct rtpn_info {
+    int N;                 /* moment order                                   */
+    int n_c;               /* (N+1)^2 components                             */
+    int n_even, n_odd;     /* components on even / odd grids (even = even l) */
+    int nx, ny, nz;
+    int bc, precision, kernel;
+    double h, dt;
+    size_t state_bytes;    /* device bytes of the moment state               */
+    size_t factor_bytes;   /* device bytes of the per-cell substep factors   */
+    long long steps_done;  /* full steps taken since the last set_moments    */
+} rtpn_info;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int rtpn_version(void);
+
+/* Static text for a status code. */
+const char* rtpn_strerror(int code);
+
+/*
+ * Component metadata (host only, no device needed).  For order N and interface index c, returns
+ * l, m, the sub-grid slots (x, y, z; each 1 or 2) and the class (0 = even grid, 1 = odd grid).
+ * Placement rule of Section 2.1: u_0 on G111 and every derivative along d switches slot d; the
+ * slots equal the reflection parities of the real basis function (slot 1 = even parity).
+ * Any output pointer may be NULL.  RTPN_EINVAL if N < 0 or c out of range.
+ */
+int rtpn_component_info(int N, int c, int* l, int* m, int slots[3], int* cls);
+
+/*
+ * Dense coupling matrix M_axis (axis 0 = x, 1 = y, 2 = z) of Eq. (3) in interface order, FP64,
+ * row-major n_c * n_c, written to caller host memory `out`.  Entries are the closed forms of
+ * int Omega_d Y_a Y_b dOmega from the Legendre ladder relations (the coefficients the kernels
+ * use).  RTPN_EINVAL if N < 0 or N > 63, axis out of range or out == NULL.
+ */
+int rtpn_coupling_dense(int N, int axis, double* out);
+
+/*
+ * Create a context for order N on nx*ny*nz cells of size h, boundary bc, storage precision, time
+ * step dt (dt <= 0 selects 0.3 h).  Allocates the state (zeroed) and the factor tables on the
+ * current CUDA device and uses the legacy default stream until rtpn_set_stream.
+ * Errors: RTPN_EINVAL (N < 0 or N > 63, dims < 1, h <= 0, bad bc/precision, out == NULL),
+ * RTPN_ECFL (dt >= h/3, Section 2.1), RTPN_ENOMEM, RTPN_ECUDA.  *out is NULL on failure.
+ */
+int rtpn_create(rtpn_ctx** out, int N, int nx, int ny, int nz, double h, int bc,
+                int precision, double dt);
+
+/* Free every device allocation of the context (after synchronising its stream). NULL is a no-op. */
+int rtpn_destroy(rtpn_ctx* ctx);
+
+/* Order all later work of the context on `stream` (a cudaStream_t; NULL = legacy default). */
+int rtpn_set_stream(rtpn_ctx* ctx, void* stream);
+
+/* Select the step kernel (RTPN_KERNEL_*) and, for RTPN_KERNEL_WINDOW, the CTA tile
+ * (tile_x * tile_y * tile_z threads, one cell each; 0 = tuned default).  RTPN_EUNSUPPORTED if
+ * the kernel is not compiled for (N, precision). */
+int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z);
+
+/*
+ * Media: per-cell sigma_a >= 0, sigma_s >= 0 and source q (added to the u_0 equation), each
+ * [z][y][x] of type dtype at `where`.  On the device, in FP64, each sub-grid point takes the mean
+ * of sigma over its 2^k adjacent cells (periodic: wrapped; vacuum: in-domain cells only), then
+ * c = sigma_a (u_0) or sigma_a + sigma_s (all others) and the factors of Eq. (5),
+ * alpha = exp(-c tau) and beta = tau E(-c tau), for tau = dt and dt/2, rounded to the storage
+ * precision.  RTPN_EINVAL on NULL or bad enums; negative sigma is not checked.
+ */
+int rtpn_set_media(rtpn_ctx* ctx, const void* sigma_a, const void* sigma_s, const void* q,
+                   int dtype, int where);
+
+/* Full state [c][z][y][x] in interface order, converted to the storage precision. */
+int rtpn_set_moments(rtpn_ctx* ctx, const void* u, int dtype, int where);
+/* Copy the full state out ([c][z][y][x], interface order) into a caller-owned buffer. */
+int rtpn_get_moments(rtpn_ctx* ctx, void* u, int dtype, int where);
+/* One component (interface index c), [z][y][x]. */
+int rtpn_set_component(rtpn_ctx* ctx, int c, const void* field, int dtype, int where);
+int rtpn_get_component(rtpn_ctx* ctx, int c, void* field, int dtype, int where);
+/* Set every moment to 0. */
+int rtpn_zero_moments(rtpn_ctx* ctx);
+
+/*
+ * Advance k >= 0 full steps of Eq. (6).  The k steps run as one odd half step, k-1 pairs of
+ * (even full step, odd full step) -- two adjacent odd half steps merged, exact because the even
+ * class is frozen between them (Eq. 5) -- then an even full step and an odd half step.
+ * Asynchronous on the context stream; the launch sequence is replayed from a cached CUDA graph.
+ * RTPN_ESTATE if media were never set.
+ */
+int rtpn_step(rtpn_ctx* ctx, int k);
+
+/*
+ * One substep S^cls_tau of Eq. (5) alone: every component of class cls (0 even, 1 odd) is advanced
+ * with the dual class frozen, tau = dt (half = 0) or dt/2 (half = 1).  rtpn_step(k) is the
+ * schedule of these passes given above; this entry lets a caller run or time a single pass.
+ * Half steps exist for the odd class only (RTPN_EINVAL for cls = 0 with half = 1).
+ * Asynchronous; RTPN_ESTATE without media.
+ */
+int rtpn_substep(rtpn_ctx* ctx, int cls, int half);
+
+/* Sum of u_0 over all cells, accumulated in FP64 in a fixed order (deterministic).
+ * Writes the host double *out; synchronises. */
+int rtpn_sum_u0(rtpn_ctx* ctx, double* out);
+
+/* Number of non-finite values in the state (host *out); synchronises.  Returns RTPN_ENONFINITE
+ * when the count is nonzero (the count is still written). */
+int rtpn_count_nonfinite(rtpn_ctx* ctx, long long* out);
+
+/* Wait for all work on the context stream. */
+int rtpn_synchronize(rtpn_ctx* ctx);
+
+/* Context facts (host struct). */
+int rtpn_get_info(const rtpn_ctx* ctx, rtpn_info* out);
+
+/* Last error message of the context ("" if none). */
+const char* rtpn_last_error(const rtpn_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTPN_H */

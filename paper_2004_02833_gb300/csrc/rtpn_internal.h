@@ -1,0 +1,103 @@
+// Internal declarations shared by the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "model.h"
+#include "rtpn.h"
+
+namespace rtpn {
+
+// ---- factor planes: per-cell FP64-computed substep factors, stored in the math precision ----
+// Eq. (5) rearranged: u' = alpha u + beta r with alpha = exp(-c tau), beta = tau E(-c tau).
+// Planes are [plane][cell]; slot code g = (gx-1) + 2(gy-1) + 4(gz-1).
+constexpr int FAC_FULL = 0;    // tau = dt:   alpha at 2g, beta at 2g+1          (planes 0..15)
+constexpr int FAC_HALF = 16;   // tau = dt/2: alpha at 16+2g, beta at 17+2g      (planes 16..31)
+constexpr int FAC_U0 = 32;     // u_0 (c = sigma_a), tau = dt: alpha, beta, beta*q (planes 32..34)
+constexpr int FAC_PLANES = 35;
+
+struct Geom {
+    int nx, ny, nz;
+    long long V;   // cells
+    int bc;        // RTPN_BC_*
+    double h;      // cell size
+};
+
+template <typename F>
+struct PartnerTable {
+    const int* row;     // [na + 1] offsets into the entries
+    const int* src;     // internal source index
+    const F* coef;      // M_d[a][b] / h, negated when the target reads its lower neighbour
+    const int* code;    // axis * 2 + (1 if the neighbour is i + 1 else 0)
+    const int* fplane;  // per target: plane of alpha (beta = next plane), FAC_U0 for u_0
+    int a0, na;         // first internal target, count
+};
+
+// host copies of the partner table of one class (built from the Model)
+struct HostTable {
+    std::vector<int> row, src, code, fplane;
+    std::vector<double> coef;
+    int a0 = 0, na = 0;
+};
+
+// ---- generic kernels (kernels_generic.cu) ----
+template <typename S, typename F>
+void launch_substep_generic(S* u, const F* fac, const PartnerTable<F>& tab, const Geom& g,
+                            int fac_ofs, cudaStream_t st);
+template <typename F>
+void launch_media_factors(const double* sa, const double* ss, const double* q, F* fac,
+                          const Geom& g, double dt, cudaStream_t st);
+template <typename Sin, typename Sout>
+void launch_convert(const Sin* in, Sout* out, long long n, cudaStream_t st);
+template <typename S>
+void launch_sum(const S* x, long long n, double* partial, int nblocks, double* out, cudaStream_t st);
+template <typename S>
+void launch_count_nonfinite(const S* x, long long n, unsigned long long* out, cudaStream_t st);
+constexpr int SUM_BLOCKS = 1024;
+
+// ---- register-window kernels (kernels_window*.cu) ----
+struct WindowLaunch {
+    void* u;                // state (float or bf16), internal order
+    const float* fac;       // factor planes
+    Geom g;
+    int cls;                // target class
+    int fac_ofs;            // FAC_FULL or FAC_HALF
+    int tx, ty, tz;         // CTA tile
+};
+// returns false if (N, precision) is not compiled in
+bool window_supported(int N, int precision);
+// uploads the coefficient constants of order N (idempotent); returns cudaError_t
+int window_prepare(const Model& md, double h, int precision);
+int launch_window(int N, int precision, const WindowLaunch& w, cudaStream_t st);
+
+}  // namespace rtpn
+
+struct rtpn_ctx {
+    rtpn::Model md;
+    rtpn::Geom g{};
+    int N = 0, prec = RTPN_FP32, kernel = RTPN_KERNEL_AUTO, active_kernel = RTPN_KERNEL_GENERIC;
+    int tx = 0, ty = 0, tz = 0;
+    double dt = 0;
+    size_t elem = 4;                 // bytes per stored moment
+    void* u = nullptr;               // state [internal c][z][y][x]
+    void* fac = nullptr;             // factor planes (double for FP64, float otherwise)
+    void* table_mem = nullptr;       // device partner tables (both classes)
+    rtpn::PartnerTable<double> tab64[2]{};
+    rtpn::PartnerTable<float> tab32[2]{};
+    double* partial = nullptr;       // reduction partials [SUM_BLOCKS] + result
+    unsigned long long* counter = nullptr;
+    void* staging = nullptr;         // one plane of FP64 (conversions, media upload)
+    double* media = nullptr;         // 3 planes of FP64 media during set_media
+    cudaStream_t stream = nullptr;   // work stream (user's or own)
+    cudaStream_t own = nullptr;      // private stream (capture, default work stream)
+    bool media_set = false;
+    long long steps_done = 0;
+    std::map<int, cudaGraphExec_t> graphs;  // pair-sequence graphs keyed by pair count
+    std::string err;
+};

@@ -1,0 +1,46 @@
+// One compiled variant of the register-window substep kernel: order RTPN_WN, target class
+// RTPN_WCLS.  The build compiles this file once per variant (each gets its own __constant__ table,
+// at most 64 KB); kernels_window.cu dispatches to them.
+#include "window_impl.cuh"
+
+#if !defined(RTPN_WN) || !defined(RTPN_WCLS)
+#error "compile with -DRTPN_WN=<order> -DRTPN_WCLS=<0|1>"
+#endif
+
+#define RTPN_CAT2(a, b, c, d) a##_##b##_##c##_##d
+#define RTPN_CAT(a, b, c, d) RTPN_CAT2(a, b, c, d)
+#define RTPN_VARIANT(name) RTPN_CAT(name, N, RTPN_WN, RTPN_WCLS)
+
+namespace rtpn {
+namespace win {
+
+constexpr int kN = RTPN_WN;
+constexpr int kA = RTPN_WCLS;
+constexpr int kSources = class_size(kN, 1 - kA);
+static_assert(kSources * 10 * 4 <= 64 * 1024 - 1024, "coefficient table exceeds constant memory");
+
+// coefficient of source j (class 1 - kA, local index) for relation k: M_d[a][b] * dir / h
+static __constant__ float c_coef[kSources * 10];
+
+template <typename S>
+__global__ void __launch_bounds__(1024, 1) k_window(Args a) {
+    substep_cell<kN, kA, S>(a, c_coef);
+}
+
+int RTPN_VARIANT(window_upload)(const float* host, int count) {
+    if (count != kSources * 10) return (int)cudaErrorInvalidValue;
+    return (int)cudaMemcpyToSymbol(c_coef, host, sizeof(float) * count);
+}
+
+int RTPN_VARIANT(window_launch)(int precision, const Args& a, cudaStream_t st) {
+    const int threads = a.tx * a.ty * a.tz;
+    const unsigned blocks = (unsigned)a.ntx * a.nty * a.ntz;
+    if (precision == RTPN_BF16)
+        k_window<__nv_bfloat16><<<blocks, threads, 0, st>>>(a);
+    else
+        k_window<float><<<blocks, threads, 0, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace win
+}  // namespace rtpn

@@ -26,3 +26,31 @@ def coupling_cache():
         return cache[N]
 
     return get
+
+
+@pytest.fixture(scope="session")
+def rtpn_lib():
+    """The built library (built in-tree on first use)."""
+    from paper_2004_02833_gb300 import build, rtpn
+
+    build.build()
+    return rtpn.lib()
+
+
+def _cuda_ok():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+@pytest.fixture(scope="session")
+def cuda_device(rtpn_lib):
+    if not _cuda_ok():
+        pytest.fail("a CUDA device is required for gpu-marked tests")
+    import torch
+
+    torch.cuda.init()
+    return torch.device("cuda:0")

@@ -1,0 +1,77 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol declared in include/*.h, and
+its host-side coefficient generator and placement agree with the oracle's quadrature (no GPU)."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import sh
+from paper_2004_02833_gb300 import rtpn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for path in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(path).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(rtpn_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_every_declared_symbol_is_exported(rtpn_lib):
+    names = declared_symbols()
+    assert len(names) >= 20
+    for name in sorted(names):
+        assert hasattr(rtpn_lib, name), name
+        assert name in rtpn.SIGNATURES, f"binding lacks {name}"
+
+
+def test_strerror_and_version(rtpn_lib):
+    assert rtpn_lib.rtpn_version() >= 100
+    assert rtpn_lib.rtpn_strerror(rtpn.ECFL).decode().startswith("time step")
+
+
+@pytest.mark.parametrize("N", [0, 1, 3, 7, 15, 39])
+def test_closed_form_coupling_matches_quadrature(rtpn_lib, coupling_cache, N):
+    # the library's ladder closed forms vs the oracle's spherical quadrature (Eq. 3)
+    (mats, slots) = coupling_cache(N)
+    for axis in range(3):
+        got = rtpn.coupling_dense(N, axis)
+        assert np.array_equal(got != 0, mats[axis] != 0), axis
+        assert np.abs(got - mats[axis]).max() < 2e-13
+
+
+@pytest.mark.parametrize("N", [1, 3, 7, 39])
+def test_component_info_matches_placement(rtpn_lib, coupling_cache, N):
+    (mats, slots) = coupling_cache(N)
+    comps = sh.components(N)
+    for c in range(len(comps)):
+        l, m, sl, cls = rtpn.component_info(N, c)
+        assert (l, m) == comps[c]
+        assert sl == tuple(slots[c])
+        assert cls == sh.parity_class(slots[c:c + 1])[0]
+
+
+def test_bad_arguments_rejected(rtpn_lib):
+    with pytest.raises(rtpn.RtpnError) as e:
+        rtpn.component_info(3, 16)
+    assert e.value.code == rtpn.EINVAL
+    with pytest.raises(rtpn.RtpnError):
+        rtpn.coupling_dense(-1, 0)
+
+
+def test_create_validates_before_touching_the_device(rtpn_lib):
+    # argument and CFL checks come first, so they hold on a machine without a GPU as well
+    with pytest.raises(rtpn.RtpnError) as e:
+        rtpn.Context(3, (4, 4, 4), 0.1, dt=0.04)
+    assert e.value.code == rtpn.ECFL
+    with pytest.raises(rtpn.RtpnError) as e:
+        rtpn.Context(-1, (4, 4, 4), 0.1)
+    assert e.value.code == rtpn.EINVAL
+    with pytest.raises(rtpn.RtpnError) as e:
+        rtpn.Context(3, (0, 4, 4), 0.1)
+    assert e.value.code == rtpn.EINVAL

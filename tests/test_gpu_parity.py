@@ -1,0 +1,154 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (stated before measuring):
+  * FP64 storage: max |u - u_ref| <= 1e-12 * max |u_ref| (the method's own bound for FP64 mode);
+  * FP32 storage: <= 1e-5 * max |u_ref| after the runs below (the FP32 bound of the target);
+  * BF16 storage (FP32 math, RNE stores): <= 2e-2 * max |u_ref|.
+"""
+import numpy as np
+import pytest
+
+from oracle import stepper as st
+from paper_2004_02833_gb300 import rtpn, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 2e-2}
+
+
+def rel_err(got, ref):
+    return float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def oracle_problem(inst, coupling_cache):
+    mats, slots = coupling_cache(inst.N)
+    return st.Problem(inst.N, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, inst.bc,
+                      mats=mats, slots=slots)
+
+
+def gpu_run(inst, u0, k, precision, kernel="auto", tile=(0, 0, 0), chunks=None):
+    with rtpn.Context(inst.N, inst.shape, inst.h, inst.bc, precision, inst.dt) as ctx:
+        if kernel != "auto":
+            ctx.set_kernel(kernel, tile)
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        if chunks is None:
+            ctx.step(k)
+        else:
+            for c in chunks:
+                ctx.step(c)
+        return ctx.get_moments()
+
+
+def test_config0_fp64_matches_oracle(cuda_device, coupling_cache):
+    # P3, 32^3 periodic, Gaussian pulse, 40 steps, FP64: <= 1e-12 relative
+    inst = synth.gaussian_pulse(3, 32)
+    u0 = inst.full_state()
+    ref = oracle_problem(inst, coupling_cache).run(u0, 40)
+    got = gpu_run(inst, u0, 40, "fp64")
+    assert rel_err(got, ref) <= TOL["fp64"]
+    assert rel_err(got[0], ref[0]) <= TOL["fp64"]
+
+
+CASES = [
+    # N, shape (nz, ny, nx), bc, steps
+    (1, (5, 6, 7), "periodic", 3),
+    (3, (9, 7, 37), "vacuum", 4),
+    (7, (23, 29, 37), "periodic", 3),
+    (7, (11, 13, 70), "vacuum", 2),
+    (15, (6, 9, 33), "periodic", 2),
+    (0, (4, 3, 5), "vacuum", 3),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("N,shape,bc,steps", CASES)
+def test_random_media_and_state(cuda_device, coupling_cache, N, shape, bc, steps, precision):
+    inst, u0 = synth.random_instance(N, shape, seed=100 + N, bc=bc)
+    ref = oracle_problem(inst, coupling_cache).run(u0, steps)
+    got = gpu_run(inst, u0, steps, precision)
+    assert rel_err(got, ref) <= TOL[precision], rel_err(got, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_generic_kernel_explicitly(cuda_device, coupling_cache, precision):
+    inst, u0 = synth.random_instance(7, (10, 12, 40), seed=7, bc="periodic")
+    ref = oracle_problem(inst, coupling_cache).run(u0, 2)
+    got = gpu_run(inst, u0, 2, precision, kernel="generic")
+    assert rel_err(got, ref) <= TOL[precision]
+
+
+def test_step_schedule_and_graph_sizes(cuda_device, coupling_cache):
+    # k = 0 leaves the state alone; k steps equal k single steps (the merged odd half steps are
+    # exact); 73 = 64 + 8 + 1 exercises every cached graph size.
+    inst, u0 = synth.random_instance(1, (4, 5, 6), seed=3, bc="vacuum")
+    P = oracle_problem(inst, coupling_cache)
+    assert rel_err(gpu_run(inst, u0, 0, "fp64"), u0) == 0.0
+    ref = P.run(u0, 73)
+    assert rel_err(gpu_run(inst, u0, 73, "fp64"), ref) <= TOL["fp64"]
+    assert rel_err(gpu_run(inst, u0, None, "fp64", chunks=[1] * 5), P.run(u0, 5)) <= TOL["fp64"]
+
+
+def test_single_cell_periodic(cuda_device, coupling_cache):
+    # 1 x 1 x 1 periodic: every neighbour is the cell itself, so all differences vanish
+    inst, u0 = synth.random_instance(3, (1, 1, 1), seed=9, bc="periodic")
+    ref = oracle_problem(inst, coupling_cache).run(u0, 4)
+    assert rel_err(gpu_run(inst, u0, 4, "fp64"), ref) <= TOL["fp64"]
+
+
+def test_conservation_on_device(cuda_device):
+    inst = synth.gaussian_pulse(3, 32)
+    for precision, tol in (("fp64", 1e-14), ("fp32", 1e-6)):
+        with rtpn.Context(3, inst.shape, inst.h, inst.bc, precision, inst.dt) as ctx:
+            ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+            ctx.set_moments(inst.full_state())
+            ctx.step(40)
+            assert abs(ctx.sum_u0() - 1.0) < tol
+            assert ctx.count_nonfinite() == 0
+
+
+def test_roundtrip_and_interface_order(cuda_device):
+    N, shape = 3, (3, 4, 5)
+    u = synth.random_state(N, shape, 1)
+    with rtpn.Context(N, shape, 0.5, "periodic", "fp64") as ctx:
+        ctx.set_moments(u)
+        assert np.array_equal(ctx.get_moments(), u)
+        ctx.zero_moments()
+        for c in (0, 5, 15):
+            ctx.set_component(c, u[c])
+            assert np.array_equal(ctx.get_component(c), u[c])
+        got = ctx.get_moments()
+        assert np.array_equal(got[[0, 5, 15]], u[[0, 5, 15]])
+        assert not got[[1, 2, 3, 4]].any()
+
+
+def test_device_buffers(cuda_device):
+    import torch
+
+    N, shape = 3, (6, 5, 4)
+    inst, u0 = synth.random_instance(N, shape, seed=2)
+    with rtpn.Context(N, shape, inst.h, inst.bc, "fp32", inst.dt) as ctx:
+        ctx.set_media(*(torch.tensor(a, device="cuda") for a in (inst.sigma_a, inst.sigma_s, inst.q)))
+        ctx.set_moments(torch.tensor(u0, device="cuda", dtype=torch.float32))
+        ctx.step(2)
+        out = torch.empty((ctx.n_c,) + shape, device="cuda", dtype=torch.float64)
+        ctx.get_moments(out)
+        ctx.synchronize()
+        host = ctx.get_moments()
+    assert np.array_equal(out.cpu().numpy(), host)
+
+
+def test_step_before_media_is_rejected(cuda_device):
+    with rtpn.Context(1, (2, 2, 2), 0.5) as ctx:
+        with pytest.raises(rtpn.RtpnError) as e:
+            ctx.step(1)
+        assert e.value.code == rtpn.ESTATE
+
+
+def test_nonfinite_detected(cuda_device):
+    N, shape = 1, (2, 2, 3)
+    u = synth.random_state(N, shape, 4)
+    u[2, 1, 1, 2] = np.nan
+    with rtpn.Context(N, shape, 0.5, "periodic", "fp32") as ctx:
+        ctx.set_moments(u)
+        assert ctx.count_nonfinite() == 1
