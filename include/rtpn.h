@@ -122,8 +122,9 @@ int rtpn_destroy(rtpn_ctx* ctx);
 int rtpn_set_stream(rtpn_ctx* ctx, void* stream);
 
 /* Select the step kernel (RTPN_KERNEL_*) and, for RTPN_KERNEL_WINDOW, the CTA tile
- * (tile_x * tile_y * tile_z threads, one cell each; 0 = tuned default).  RTPN_EUNSUPPORTED if
- * the kernel is not compiled for (N, precision). */
+ * (tile_x * tile_y * tile_z threads, one cell each; a 0 takes the default 32 x 4 x 2).  The tile
+ * must hold a multiple of 32 threads, at most 256 (RTPN_EINVAL).  RTPN_EUNSUPPORTED if the kernel
+ * is not compiled for (N, precision); the previous selection then stays. */
 int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z);
 
 /*

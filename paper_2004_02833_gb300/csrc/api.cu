@@ -415,8 +415,13 @@ int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_
     if (!ctx) return RTPN_EINVAL;
     if (kernel < RTPN_KERNEL_AUTO || kernel > RTPN_KERNEL_WINDOW)
         return fail(ctx, RTPN_EINVAL, "unknown kernel");
-    if (tile_x < 0 || tile_y < 0 || tile_z < 0 || (long long)tile_x * tile_y * tile_z > 1024)
-        return fail(ctx, RTPN_EINVAL, "bad tile");
+    if (tile_x < 0 || tile_y < 0 || tile_z < 0) return fail(ctx, RTPN_EINVAL, "bad tile");
+    if (tile_x || tile_y || tile_z) {
+        const long long th = (long long)(tile_x ? tile_x : 32) * (tile_y ? tile_y : 4) *
+                             (tile_z ? tile_z : 2);
+        if (th > 256 || th % 32 != 0)
+            return fail(ctx, RTPN_EINVAL, "tile must hold a multiple of 32 threads, at most 256");
+    }
     const int old = ctx->kernel;
     ctx->kernel = kernel;
     if (tile_x != ctx->tx || tile_y != ctx->ty || tile_z != ctx->tz) drop_graphs(ctx);

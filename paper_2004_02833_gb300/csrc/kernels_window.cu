@@ -39,40 +39,6 @@ static const Variant* find(int N) {
     return nullptr;
 }
 
-// Coefficient table of target class A: for every source j of class 1 - A (internal order) and
-// relation k, M_d[a][b] * dir.  Cross-checks the compile-time relations against the model's
-// nonzeros; returns false on any mismatch.
-static bool coef_table(const Model& md, int A, std::vector<float>* out) {
-    const int N = md.N, B = 1 - A;
-    const int base = B == 0 ? 0 : md.ne;
-    const int nS = class_size(N, B);
-    if (nS != (B == 0 ? md.ne : md.no)) return false;
-    std::unordered_map<long long, std::pair<int, double>> nz;
-    long long expected = 0;
-    for (const auto& e : md.nz) {
-        nz[(long long)e.a * md.nc + e.b] = {e.axis, e.v};
-        if (md.comp[e.b].cls == B) ++expected;
-    }
-    out->assign((size_t)nS * 10, 0.f);
-    long long found = 0;
-    for (int j = 0; j < nS; ++j) {
-        const int b = md.abi_of_internal[base + j];
-        const Component& c = md.comp[b];
-        if (local_index(N, B, c.l, c.M, c.t) != j) return false;
-        for (int k = 0; k < 10; ++k) {
-            const Target T = relation(N, c.l, c.M, c.t, k);
-            if (!T.ok) continue;
-            const int a = abi_index(T.l, T.M, T.t);
-            auto it = nz.find((long long)a * md.nc + b);
-            if (it == nz.end() || it->second.first != T.axis) return false;
-            const double dir = c.slot[T.axis] == 1 ? 1.0 : -1.0;
-            (*out)[(size_t)j * 10 + k] = (float)(it->second.second * dir);
-            ++found;
-        }
-    }
-    return found == expected;
-}
-
 }  // namespace win
 
 bool window_supported(int N, int precision) {
@@ -115,7 +81,7 @@ int launch_window(int N, int precision, const WindowLaunch& w, cudaStream_t st) 
     a.tx = w.tx > 0 ? w.tx : 32;
     a.ty = w.ty > 0 ? w.ty : 4;
     a.tz = w.tz > 0 ? w.tz : 2;
-    if (a.tx * a.ty * a.tz > 1024 || (a.tx * a.ty * a.tz) % 32 != 0) return (int)cudaErrorInvalidValue;
+    if (a.tx * a.ty * a.tz > 256 || (a.tx * a.ty * a.tz) % 32 != 0) return (int)cudaErrorInvalidValue;
     a.ntx = (a.nx + a.tx - 1) / a.tx;
     a.nty = (a.ny + a.ty - 1) / a.ty;
     a.ntz = (a.nz + a.tz - 1) / a.tz;

@@ -23,8 +23,10 @@ static_assert(kSources * 10 * 4 <= 64 * 1024 - 1024, "coefficient table exceeds 
 static __constant__ float c_coef[kSources * 10];
 
 template <typename S>
-__global__ void __launch_bounds__(1024, 1) k_window(Args a) {
-    substep_cell<kN, kA, S>(a, c_coef);
+__global__ void __launch_bounds__(256) k_window(Args a) {
+    int x, y, z;
+    if (!cell_of(a, blockIdx.x, threadIdx.x, &x, &y, &z)) return;
+    substep_cell<kN, kA, S>(a, c_coef, x, y, z);
 }
 
 int RTPN_VARIANT(window_upload)(const float* host, int count) {

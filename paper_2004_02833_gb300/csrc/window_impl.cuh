@@ -19,7 +19,9 @@
 #include <cuda_bf16.h>
 
 #include <type_traits>
+#include <unordered_map>
 #include <utility>
+#include <vector>
 
 #include "rtpn_internal.h"
 
@@ -94,29 +96,55 @@ __host__ __device__ constexpr bool needs_axis(int N, int l, int M, int t, int ax
 }
 
 // ---------------------------------------------------------------- compile-time loops
+// The per-cell body is __host__ __device__ so that the same code can be run over a grid on the
+// host (with bounds-checked memory) when checking it; on the device, loads of the frozen class and
+// of the factors go through the read-only path.
+#define RTPN_HD __host__ __device__ __forceinline__
+
 template <typename F, int... Is>
-__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>) {
+RTPN_HD void static_for_impl(F&& f, std::integer_sequence<int, Is...>) {
     (f(std::integral_constant<int, Is>{}), ...);
 }
 template <int Count, typename F>
-__device__ __forceinline__ void static_for(F&& f) {
+RTPN_HD void static_for(F&& f) {
     static_for_impl(f, std::make_integer_sequence<int, Count>{});
 }
 
-template <typename S>
-__device__ __forceinline__ float load_nc(const S* p);
-template <>
-__device__ __forceinline__ float load_nc<float>(const float* p) { return __ldg(p); }
-template <>
-__device__ __forceinline__ float load_nc<__nv_bfloat16>(const __nv_bfloat16* p) {
-    return __bfloat162float(__ldg(p));
+#ifndef RTPN_HOST_CHECK
+#define RTPN_CHECK_PTR(p) ((void)0)
+#endif
+
+RTPN_HD float ro(const float* p) {
+    RTPN_CHECK_PTR(p);
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
 }
 template <typename S>
-__device__ __forceinline__ void store(S* p, float v);
+RTPN_HD float load_nc(const S* p);
 template <>
-__device__ __forceinline__ void store<float>(float* p, float v) { *p = v; }
+RTPN_HD float load_nc<float>(const float* p) { return ro(p); }
 template <>
-__device__ __forceinline__ void store<__nv_bfloat16>(__nv_bfloat16* p, float v) {
+RTPN_HD float load_nc<__nv_bfloat16>(const __nv_bfloat16* p) {
+    RTPN_CHECK_PTR(p);
+#ifdef __CUDA_ARCH__
+    return __bfloat162float(__ldg(p));
+#else
+    return __bfloat162float(*p);
+#endif
+}
+template <typename S>
+RTPN_HD void store(S* p, float v);
+template <>
+RTPN_HD void store<float>(float* p, float v) {
+    RTPN_CHECK_PTR(p);
+    *p = v;
+}
+template <>
+RTPN_HD void store<__nv_bfloat16>(__nv_bfloat16* p, float v) {
+    RTPN_CHECK_PTR(p);
     *p = __float2bfloat16_rn(v);
 }
 
@@ -133,19 +161,23 @@ struct Args {
 
 // coef[j * 10 + k]: source j (local index in class B), relation k: M_d[a][b] * dir, where dir = +1 if
 // the source is read at i + e_d and -1 if at i - e_d; r = -(1/h) * sum coef * (u(neighbour) - u(i)).
-template <int N, int A, typename S>
-__device__ __forceinline__ void substep_cell(const Args& a, const float* __restrict__ coef) {
-    constexpr int B = 1 - A;
-    constexpr int NL = N / 2 + 1;
-    // ---- which cell
-    const int tid = threadIdx.x;
+// Cell of thread `tid` in block `blk`: tiles are ordered with z fastest, so consecutive blocks are
+// z-neighbours and share their planes through L2.
+RTPN_HD bool cell_of(const Args& a, int blk, int tid, int* x, int* y, int* z) {
     const int lx = tid % a.tx, ly = (tid / a.tx) % a.ty, lz = tid / (a.tx * a.ty);
-    const int blk = blockIdx.x;
     const int bz = blk % a.ntz;
     const int rest = blk / a.ntz;
     const int bx = rest % a.ntx, by = rest / a.ntx;
-    const int x = bx * a.tx + lx, y = by * a.ty + ly, z = bz * a.tz + lz;
-    if (x >= a.nx || y >= a.ny || z >= a.nz) return;
+    *x = bx * a.tx + lx;
+    *y = by * a.ty + ly;
+    *z = bz * a.tz + lz;
+    return *x < a.nx && *y < a.ny && *z < a.nz;
+}
+
+template <int N, int A, typename S>
+RTPN_HD void substep_cell(const Args& a, const float* __restrict__ coef, int x, int y, int z) {
+    constexpr int B = 1 - A;
+    constexpr int NL = N / 2 + 1;
     const long long V = a.V;
     const long long cell = ((long long)z * a.ny + y) * a.nx + x;
     const bool periodic = a.bc == RTPN_BC_PERIODIC;
@@ -179,15 +211,15 @@ __device__ __forceinline__ void substep_cell(const Args& a, const float* __restr
         constexpr int g = decltype(gi)::value;
         constexpr int twos = (g & 1) + ((g >> 1) & 1) + ((g >> 2) & 1);
         if constexpr (twos % 2 == A) {
-            al[g] = __ldg(a.fac + (long long)(a.fac_ofs + 2 * g) * V + cell);
-            be[g] = __ldg(a.fac + (long long)(a.fac_ofs + 2 * g + 1) * V + cell) * a.inv_h;
+            al[g] = ro(a.fac + (long long)(a.fac_ofs + 2 * g) * V + cell);
+            be[g] = ro(a.fac + (long long)(a.fac_ofs + 2 * g + 1) * V + cell) * a.inv_h;
         }
     });
     float al0 = 0.f, be0 = 0.f, ga0 = 0.f;
     if constexpr (A == 0) {
-        al0 = __ldg(a.fac + (long long)FAC_U0 * V + cell);
-        be0 = __ldg(a.fac + (long long)(FAC_U0 + 1) * V + cell) * a.inv_h;
-        ga0 = __ldg(a.fac + (long long)(FAC_U0 + 2) * V + cell);
+        al0 = ro(a.fac + (long long)FAC_U0 * V + cell);
+        be0 = ro(a.fac + (long long)(FAC_U0 + 1) * V + cell) * a.inv_h;
+        ga0 = ro(a.fac + (long long)(FAC_U0 + 2) * V + cell);
     }
 
     float acc[3][2][NL];
@@ -266,6 +298,40 @@ __device__ __forceinline__ void substep_cell(const Args& a, const float* __restr
         if constexpr (Ms >= 1) finalize(std::integral_constant<int, Ms - 1>{});
         if constexpr (Ms == N) finalize(std::integral_constant<int, N>{});
     });
+}
+
+// Coefficient table of target class A: for every source j of class 1 - A (internal order) and
+// relation k, M_d[a][b] * dir.  Cross-checks the compile-time relations against the model's
+// nonzeros; returns false on any mismatch.
+inline bool coef_table(const Model& md, int A, std::vector<float>* out) {
+    const int N = md.N, B = 1 - A;
+    const int base = B == 0 ? 0 : md.ne;
+    const int nS = class_size(N, B);
+    if (nS != (B == 0 ? md.ne : md.no)) return false;
+    std::unordered_map<long long, std::pair<int, double>> nz;
+    long long expected = 0;
+    for (const auto& e : md.nz) {
+        nz[(long long)e.a * md.nc + e.b] = {e.axis, e.v};
+        if (md.comp[e.b].cls == B) ++expected;
+    }
+    out->assign((size_t)nS * 10, 0.f);
+    long long found = 0;
+    for (int j = 0; j < nS; ++j) {
+        const int b = md.abi_of_internal[base + j];
+        const Component& c = md.comp[b];
+        if (local_index(N, B, c.l, c.M, c.t) != j) return false;
+        for (int k = 0; k < 10; ++k) {
+            const Target T = relation(N, c.l, c.M, c.t, k);
+            if (!T.ok) continue;
+            const int a = abi_index(T.l, T.M, T.t);
+            auto it = nz.find((long long)a * md.nc + b);
+            if (it == nz.end() || it->second.first != T.axis) return false;
+            const double dir = c.slot[T.axis] == 1 ? 1.0 : -1.0;
+            (*out)[(size_t)j * 10 + k] = (float)(it->second.second * dir);
+            ++found;
+        }
+    }
+    return found == expected;
 }
 
 }  // namespace win

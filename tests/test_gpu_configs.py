@@ -1,0 +1,101 @@
+"""The workloads at their full sizes, in the launch configuration bench.py times.
+
+Where the oracle cannot run the whole workload, it computes one step from the same state at full
+size (its cost is seconds), and long runs are compared with the GPU FP64 path, which the small
+cases pin to the oracle at <= 1e-12.  Comparisons of large states are done component by component
+on the device (torch is only the comparison plumbing here).
+"""
+import numpy as np
+import pytest
+
+from oracle import stepper as st
+from paper_2004_02833_gb300 import rtpn, synth
+
+from test_gpu_parity import bf16_tol
+
+pytestmark = pytest.mark.gpu
+
+
+def make(inst, precision, kernel="auto"):
+    ctx = rtpn.Context(inst.N, inst.shape, inst.h, inst.bc, precision, inst.dt)
+    if kernel != "auto":
+        ctx.set_kernel(kernel)
+    ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+    return ctx
+
+
+def device_rel_err(a, b, n_c, shape):
+    """max |a - b| / max |b| over the full state, one component at a time on the device."""
+    import torch
+
+    ta = torch.empty(shape, dtype=torch.float64, device="cuda")
+    tb = torch.empty(shape, dtype=torch.float64, device="cuda")
+    num, den, num0, den0 = 0.0, 0.0, 0.0, 0.0
+    for c in range(n_c):
+        a.get_component(c, ta)
+        b.get_component(c, tb)
+        a.synchronize()
+        b.synchronize()
+        d = float((ta - tb).abs().max())
+        r = float(tb.abs().max())
+        num, den = max(num, d), max(den, r)
+        if c == 0:
+            num0, den0 = d, r
+    return num / den, num0 / den0
+
+
+def test_config1_one_step_vs_oracle_full_size(cuda_device):
+    # P7, 128^3 checkerboard lattice, vacuum: one step from a dense random state, whole grid
+    inst = synth.checkerboard(7, 128)
+    u0 = synth.random_state(7, inst.shape, 5)
+    ref = st.Problem(7, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, inst.bc).step(u0)
+    for precision, tol in (("fp64", 1e-12), ("fp32", 1e-5)):
+        with make(inst, precision) as ctx:
+            ctx.set_moments(u0)
+            ctx.step(1)
+            got = ctx.get_moments()
+        assert np.abs(got - ref).max() / np.abs(ref).max() <= tol, precision
+
+
+def test_config1_200_steps_fp32_vs_fp64(cuda_device):
+    # P7 128^3 checkerboard, source in the central block, zero initial state, 200 steps
+    inst = synth.checkerboard(7, 128)
+    with make(inst, "fp64") as ref, make(inst, "fp32") as got:
+        ref.step(200)
+        got.step(200)
+        err, err0 = device_rel_err(got, ref, 64, inst.shape)
+        assert ref.count_nonfinite() == 0 and got.count_nonfinite() == 0
+    assert err <= 1e-5 and err0 <= 1e-5, (err, err0)
+
+
+def test_config2_small_instance_vs_oracle(cuda_device):
+    # P39 on an independent 24^3 instance with the 200^3 rules, 100 steps: GPU FP64 vs the oracle
+    inst = synth.random_blocks(39, 24, seed=2)
+    u0 = inst.full_state()
+    ref = st.Problem(39, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, inst.bc).run(u0, 100)
+    for precision, tol in (("fp64", 1e-12), ("fp32", 1e-5), ("bf16", bf16_tol(100))):
+        with make(inst, precision) as ctx:
+            ctx.set_moments(u0)
+            ctx.step(100)
+            got = ctx.get_moments()
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= tol, (precision, err)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", bf16_tol(100))])
+def test_config2_full_size_vs_gpu_fp64(cuda_device, precision, tol):
+    # P39 200^3 periodic, 100 steps: FP32 / BF16 storage vs the GPU FP64 path on the same input
+    import torch
+
+    inst = synth.random_blocks(39, 200, seed=2)
+    u0 = torch.tensor(inst.u0, device="cuda")
+    with make(inst, "fp64") as ref:
+        ref.set_component(0, u0)
+        ref.step(100)
+        with make(inst, precision) as got:
+            got.set_component(0, u0)
+            got.step(100)
+            err, err0 = device_rel_err(got, ref, 1600, inst.shape)
+            s_ref, s_got = ref.sum_u0(), got.sum_u0()
+    assert err <= tol and err0 <= tol, (err, err0)
+    assert abs(s_got - s_ref) <= tol * abs(s_ref)
