@@ -174,6 +174,24 @@ int rtpn_sum_u0(rtpn_ctx* ctx, double* out);
  * when the count is nonzero (the count is still written). */
 int rtpn_count_nonfinite(rtpn_ctx* ctx, long long* out);
 
+/*
+ * FP64 sum of n values of a device array x (dtype RTPN_DTYPE_F64 or RTPN_DTYPE_F32), written to the
+ * device double *out, ordered on `stream` (a cudaStream_t; NULL = legacy default stream).  The
+ * paper has no counterpart; this entry point is for callers that cannot allocate device memory at
+ * the point where they need a sum -- code running while a framework's caching pool owns the
+ * device memory (a private cudaMalloc can fail there or fragment the pool), or a time-critical
+ * loop where cudaMalloc / cudaFree would synchronise the whole device.  It allocates nothing: its
+ * scratch is a file-scope device array of 2^16 FP64 partial sums (512 KB) that every GPU which
+ * loads this library holds until the process exits, so n is limited to 2^30 values (RTPN_EINVAL
+ * beyond, with the reason in rtpn_last_error(NULL)).  The sum is taken in a fixed order and is
+ * reproducible.  The first call on a device looks up the scratch's device address, so make that
+ * first call before any stream capture.  Every call shares the one scratch array and each call
+ * overwrites the partials it reads (nothing has to start at zero); calls that overlap on the GPU
+ * (on streams with no ordering between them) race and give wrong sums.  Asynchronous; RTPN_EINVAL
+ * on NULL pointers, n < 0 or a bad dtype; RTPN_ECUDA if a launch fails.
+ */
+int rtpn_sum_static(const void* x, int dtype, long long n, double* out, void* stream);
+
 /* Wait for all work on the context stream. */
 int rtpn_synchronize(rtpn_ctx* ctx);
 

@@ -293,6 +293,11 @@ int choose_kernel(rtpn_ctx* ctx) {
 
 }  // namespace
 
+namespace rtpn {
+// Message for rtpn_last_error(NULL) from entry points that take no context.
+void note_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace rtpn
+
 // ==================================================================== C ABI
 extern "C" {
 

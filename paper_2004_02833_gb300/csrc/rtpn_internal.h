@@ -46,6 +46,9 @@ struct HostTable {
     int a0 = 0, na = 0;
 };
 
+// message for rtpn_last_error(NULL) (entry points without a context)
+void note_error(const std::string& msg);
+
 // ---- generic kernels (kernels_generic.cu) ----
 template <typename S, typename F>
 void launch_substep_generic(S* u, const F* fac, const PartnerTable<F>& tab, const Geom& g,

@@ -61,6 +61,7 @@ SIGNATURES = {
     "rtpn_substep": (_I, [_P, _I, _I]),
     "rtpn_sum_u0": (_I, [_P, ctypes.POINTER(_D)]),
     "rtpn_count_nonfinite": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "rtpn_sum_static": (_I, [_P, _I, ctypes.c_longlong, _P, _P]),
     "rtpn_synchronize": (_I, [_P]),
     "rtpn_get_info": (_I, [_P, ctypes.POINTER(Info)]),
     "rtpn_last_error": (ctypes.c_char_p, [_P]),
@@ -124,6 +125,23 @@ def coupling_dense(N: int, axis: int) -> np.ndarray:
     n = (N + 1) ** 2
     out = np.zeros((n, n), dtype=np.float64)
     _check(lib().rtpn_coupling_dense(N, axis, out.ctypes.data))
+    return out
+
+
+def sum_static(x, out, stream=None):
+    """FP64 sum of the device tensor x (float32/float64) into the one-element device float64 tensor
+    out, without any allocation by the library (see rtpn_sum_static in include/rtpn.h)."""
+    import torch
+
+    if not (x.is_cuda and out.is_cuda and out.dtype == torch.float64 and x.is_contiguous()):
+        raise ValueError("x must be a contiguous CUDA tensor and out a CUDA float64 tensor")
+    code = DTYPE_F64 if x.dtype == torch.float64 else DTYPE_F32
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = getattr(stream, "cuda_stream", stream)
+    rc = lib().rtpn_sum_static(_P(x.data_ptr()), code, x.numel(), _P(out.data_ptr()), _P(handle or 0))
+    if rc != OK:
+        raise RtpnError(rc, lib().rtpn_last_error(None).decode() or lib().rtpn_strerror(rc).decode())
     return out
 
 
