@@ -67,6 +67,8 @@ extern "C" {
 #define RTPN_KERNEL_AUTO    0  /* fastest available for (N, precision)                            */
 #define RTPN_KERNEL_GENERIC 1  /* any N and precision: one thread per cell, partner-table gather   */
 #define RTPN_KERNEL_WINDOW  2  /* FP32/BF16, compiled N: register-window scatter over m-columns  */
+#define RTPN_KERNEL_STAGE   3  /* FP32/BF16, compiled N, nx*elem a multiple of 16 B: column loop
+                                  with TMA-staged shared-memory tiles, persistent CTAs          */
 
 typedef struct rtpn_ctx rtpn_ctx;
 
@@ -121,10 +123,12 @@ int rtpn_destroy(rtpn_ctx* ctx);
 /* Order all later work of the context on `stream` (a cudaStream_t; NULL = legacy default). */
 int rtpn_set_stream(rtpn_ctx* ctx, void* stream);
 
-/* Select the step kernel (RTPN_KERNEL_*) and, for RTPN_KERNEL_WINDOW, the CTA tile
- * (tile_x * tile_y * tile_z threads, one cell each; a 0 takes the default 32 x 4 x 2).  The tile
- * must hold a multiple of 32 threads, at most 256 (RTPN_EINVAL).  RTPN_EUNSUPPORTED if the kernel
- * is not compiled for (N, precision); the previous selection then stays. */
+/* Select the step kernel (RTPN_KERNEL_*) and its CTA tile (tile_x * tile_y * tile_z threads, one
+ * cell each; all 0 = default).  RTPN_KERNEL_WINDOW: the tile must hold a multiple of 32 threads, at
+ * most 256 (RTPN_EINVAL); default 32 x 4 x 2.  RTPN_KERNEL_STAGE: the tile must be one compiled for
+ * N (RTPN_EUNSUPPORTED otherwise).  RTPN_KERNEL_AUTO picks STAGE, then WINDOW, then GENERIC.
+ * RTPN_EUNSUPPORTED if the kernel is not compiled for (N, precision, nx); the previous selection
+ * then stays. */
 int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z);
 
 /*
@@ -192,8 +196,82 @@ int rtpn_count_nonfinite(rtpn_ctx* ctx, long long* out);
  */
 int rtpn_sum_static(const void* x, int dtype, long long n, double* out, void* stream);
 
-/* Wait for all work on the context stream. */
+/*
+ * Discrete adjoint (gradients of a detector functional).  Starting from the context's current state
+ * u(0) and media, runs k steps of Eq. (6) taken literally (odd half, even full, odd half substeps;
+ * the schedule the oracle's discrete adjoint transposes) and returns
+ *     J = sum over cells of w * u_0(after k steps)          (host double *J)
+ * and dJ/dsigma_a, dJ/dsigma_s, dJ/dq per cell ([z][y][x], FP64, host or device per out_where).
+ * Each substep u_A' = alpha u_A + beta r_A (Eq. 5) is pulled back exactly: lam_A <- alpha lam_A,
+ * lam_B <- lam_B - K^T (beta lam_A) with the transposed staggered stencil, and the media collect
+ * lam (dalpha/dc u + dbeta/dc r) at the staggered points, spread to the cells through the
+ * transpose of the point mean, plus beta_0 lam_0 for q.  States are checkpointed every ckpt_every
+ * steps and each segment is recomputed forward with its pre-substep states kept on the device
+ * (device memory ~ (k/ckpt_every + 3 ckpt_every) states).  w is [z][y][x] of dtype at `where`.
+ * Afterwards the context holds u(k).  FP64 and FP32 storage (RTPN_EUNSUPPORTED for BF16);
+ * RTPN_ESTATE without media; RTPN_ENOMEM if the checkpoints do not fit.  Synchronises.
+ */
+int rtpn_adjoint(rtpn_ctx* ctx, const void* w, int dtype, int where, int k, int ckpt_every,
+                 double* g_sa, double* g_ss, double* g_q, int out_where, double* J);
+
+/* ======================================================================== batched form
+ * Many independent instances of uneven order N and grid size advanced together.  Each pass of the
+ * merged Strang schedule (see rtpn_step) is ONE persistent kernel launch over the tiles of every
+ * instance (CTAs draw tiles from a work counter, largest orders first); k-step sequences are
+ * replayed from cached CUDA graphs.  Storage FP32 or BF16; orders 1, 3, 5, 7, 9, 15.
+ */
+typedef struct rtpn_batch rtpn_batch;
+
+/* Create `count` instances: per-instance arrays N, nx, ny, nz, h, bc and dt (dt may be NULL:
+ * 0.3 h each).  Every instance gets its own context (see rtpn_batch_instance).
+ * RTPN_EUNSUPPORTED for an order outside {1,3,5,7,9,15} or precision RTPN_FP64; otherwise the
+ * errors of rtpn_create.  *out is NULL on failure. */
+int rtpn_batch_create(rtpn_batch** out, int count, const int* N, const int* nx, const int* ny,
+                      const int* nz, const double* h, const int* bc, const double* dt,
+                      int precision);
+int rtpn_batch_destroy(rtpn_batch* b);
+/* Number of instances (RTPN_EINVAL for NULL). */
+int rtpn_batch_count(const rtpn_batch* b);
+/* The context of instance i, owned by the batch (do not destroy it): use it for set_media,
+ * set/get_moments, sum_u0 and the other per-instance calls.  NULL if i is out of range. */
+rtpn_ctx* rtpn_batch_instance(rtpn_batch* b, int i);
+/* Order the batch's work (and every instance's) on `stream` (NULL = the batch's own stream). */
+int rtpn_batch_set_stream(rtpn_batch* b, void* stream);
+/* CTA tile of the grouped kernel (threads a multiple of 32, at most 256); default 32 x 4 x 2. */
+int rtpn_batch_set_tile(rtpn_batch* b, int tile_x, int tile_y, int tile_z);
+int rtpn_batch_get_tile(const rtpn_batch* b, int* tile_x, int* tile_y, int* tile_z);
+/* Advance every instance k steps with one grouped launch per pass.  RTPN_ESTATE if some instance
+ * has no media. */
+int rtpn_batch_step(rtpn_batch* b, int k);
+/* The same k steps as a loop of per-instance launches of the single-instance kernel (the
+ * comparison baseline for the grouped launch). */
+int rtpn_batch_step_looped(rtpn_batch* b, int k);
+int rtpn_batch_synchronize(rtpn_batch* b);
+const char* rtpn_batch_last_error(const rtpn_batch* b);
+
+/* ======================================================================== autotuner
+ * Pick the CTA tile of the register-window kernel by timing candidate tiles (a multiple of 32
+ * threads, at most 256) on the object's own data; the state is copied aside first and restored, so
+ * the moments are unchanged (needs device memory for one copy of the state: RTPN_ENOMEM if absent).
+ * The best tile is applied, written to tile[3] and its time to *ms (one even + odd pass pair for a
+ * context, one rtpn_batch_step(b, 1) for a batch); either output may be NULL.  Results are cached
+ * for the process per (orders, precision, boundary, grid, device) and, when the environment
+ * variable RTPN_TUNE_CACHE names a file, kept there across processes.  Synchronises.
+ * RTPN_ESTATE without media; RTPN_EUNSUPPORTED if the window kernel is not active.
+ */
+int rtpn_autotune(rtpn_ctx* ctx, int reps, int tile[3], double* ms);
+int rtpn_batch_autotune(rtpn_batch* b, int reps, int tile[3], double* ms);
+
+/* Wait for all work on the context stream.  Returns RTPN_ETIMEOUT (and clears the flag) if a
+ * bounded wait inside a staged kernel ran out since the last check; the context stays usable, but
+ * the state of the pass that timed out is undefined (reload it). */
 int rtpn_synchronize(rtpn_ctx* ctx);
+
+/* Test hook for the timeout path: one staged pass of class cls in which one stage's copies are
+ * deliberately never issued, with `wait_limit` mbarrier polls, so every CTA's bounded wait must run
+ * out, set the status word and leave.  The next rtpn_synchronize returns RTPN_ETIMEOUT.  Leaves the
+ * state undefined.  RTPN_EUNSUPPORTED unless the staged kernel is active. */
+int rtpn_test_wait_timeout(rtpn_ctx* ctx, int cls, long long wait_limit);
 
 /* Context facts (host struct). */
 int rtpn_get_info(const rtpn_ctx* ctx, rtpn_info* out);

@@ -32,6 +32,7 @@ def _nvcc() -> str:
 
 
 VARIANT_SRC = "window.cu"  # compiled once per (order, class) listed in window_variants.h
+STAGE_SRC = "stage.cu"     # compiled once per (order, tile) listed in stage_variants.h
 
 
 def window_orders() -> list[int]:
@@ -40,17 +41,28 @@ def window_orders() -> list[int]:
     return [int(v) for v in re.findall(r"X\((\d+)\)", line)]
 
 
+def stage_variants() -> list[tuple[int, int, int, int]]:
+    text = open(os.path.join(CSRC, "stage_variants.h")).read()
+    line = [l for l in text.splitlines() if l.startswith("#define RTPN_STAGE_VARIANTS")][0]
+    return [tuple(int(v) for v in m) for m in
+            re.findall(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", line)]
+
+
 def units() -> list[tuple[str, list[str], str]]:
     """(source, defines, object name) of every translation unit."""
     out = []
     for f in sorted(os.listdir(CSRC)):
-        if not f.endswith((".cu", ".cpp")) or f == VARIANT_SRC:
+        if not f.endswith((".cu", ".cpp")) or f in (VARIANT_SRC, STAGE_SRC):
             continue
         out.append((os.path.join(CSRC, f), [], f + ".o"))
     for n in window_orders():
         for cls in (0, 1):
             out.append((os.path.join(CSRC, VARIANT_SRC), [f"-DRTPN_WN={n}", f"-DRTPN_WCLS={cls}"],
                         f"window_N{n}_c{cls}.o"))
+    for n, tx, ty, tz in stage_variants():
+        out.append((os.path.join(CSRC, STAGE_SRC),
+                    [f"-DRTPN_SN={n}", f"-DRTPN_STX={tx}", f"-DRTPN_STY={ty}", f"-DRTPN_STZ={tz}"],
+                    f"stage_N{n}_{tx}x{ty}x{tz}.o"))
     return out
 
 
@@ -74,7 +86,8 @@ def build(verbose: bool = False, extra: list[str] | None = None, jobs: int | Non
     extra = list(extra or [])
     todo = units()
     # longest units first so the parallel build ends sooner
-    todo.sort(key=lambda u: -max([int(d.split("=")[1]) for d in u[1] if "RTPN_WN" in d] or [0]))
+    todo.sort(key=lambda u: -max([int(d.split("=")[1]) for d in u[1]
+                                  if d.startswith(("-DRTPN_WN", "-DRTPN_SN"))] or [0]))
     jobs = jobs or min(len(todo), max(2, os.cpu_count() or 2))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda u: _compile(u, extra), todo))

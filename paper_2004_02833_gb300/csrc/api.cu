@@ -126,7 +126,11 @@ int take_component(rtpn_ctx* ctx, int abi, void* dst, int dtype, int where) {
 
 // ------------------------------------------------------------------ step schedule
 int run_pass(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st) {
-    if (ctx->active_kernel == RTPN_KERNEL_WINDOW) {
+    if (ctx->active_kernel == RTPN_KERNEL_STAGE) {
+        int rc = launch_stage(ctx, cls, fac_ofs, st, -1, STAGE_WAIT_LIMIT);
+        if (rc) return fail(ctx, RTPN_ECUDA, std::string("staged kernel: ") +
+                                                 cudaGetErrorString((cudaError_t)rc));
+    } else if (ctx->active_kernel == RTPN_KERNEL_WINDOW) {
         WindowLaunch w;
         w.u = ctx->u;
         w.fac = (const float*)ctx->fac;
@@ -268,6 +272,14 @@ void release(rtpn_ctx* ctx) {
     if (ctx->partial) cudaFree(ctx->partial);
     if (ctx->counter) cudaFree(ctx->counter);
     if (ctx->staging) cudaFree(ctx->staging);
+    if (ctx->status) cudaFree(ctx->status);
+    if (ctx->media) cudaFree(ctx->media);
+    ctx->media = nullptr;
+    if (ctx->stage_mem) cudaFree(ctx->stage_mem);
+    if (ctx->stage_maps_dev) cudaFree(ctx->stage_maps_dev);
+    ctx->stage_maps_dev = nullptr;
+    ctx->status = nullptr;
+    ctx->stage_mem = nullptr;
     if (ctx->own) cudaStreamDestroy(ctx->own);
     ctx->u = ctx->fac = ctx->table_mem = ctx->staging = nullptr;
     ctx->partial = nullptr;
@@ -275,10 +287,29 @@ void release(rtpn_ctx* ctx) {
     ctx->own = nullptr;
 }
 
+// The staged kernel joins automatic selection once it has passed its GPU tests.
+constexpr bool kStageInAuto = false;
+
 int choose_kernel(rtpn_ctx* ctx) {
     int k = ctx->kernel;
-    if (k == RTPN_KERNEL_AUTO)
-        k = window_supported(ctx->N, ctx->prec) ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
+    if (k == RTPN_KERNEL_AUTO) {
+        const bool tile_set = ctx->tx || ctx->ty || ctx->tz;
+        if (kStageInAuto && stage_supported(ctx->N, ctx->prec, ctx->g.nx) &&
+            (!tile_set || stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz)))
+            k = RTPN_KERNEL_STAGE;
+        else
+            k = window_supported(ctx->N, ctx->prec) ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
+    }
+    if (k == RTPN_KERNEL_STAGE) {
+        if (!stage_supported(ctx->N, ctx->prec, ctx->g.nx))
+            return fail(ctx, RTPN_EUNSUPPORTED,
+                        "staged kernel not compiled for this N/precision or nx*elem not 16-byte rows");
+        if ((ctx->tx || ctx->ty || ctx->tz) && !stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz))
+            return fail(ctx, RTPN_EUNSUPPORTED, "no staged kernel compiled for this tile");
+        int rc = stage_prepare(ctx, ctx->tx, ctx->ty, ctx->tz);
+        if (rc) return fail(ctx, RTPN_ECUDA, std::string("staged kernel set-up: ") +
+                                                 cudaGetErrorString((cudaError_t)rc));
+    }
     if (k == RTPN_KERNEL_WINDOW) {
         if (!window_supported(ctx->N, ctx->prec))
             return fail(ctx, RTPN_EUNSUPPORTED, "window kernel not compiled for this N/precision");
@@ -392,6 +423,10 @@ int rtpn_create(rtpn_ctx** out, int N, int nx, int ny, int nz, double h, int bc,
     if (e != cudaSuccess) return bail(fail(ctx, RTPN_ENOMEM, "scratch allocation failed"));
     e = cudaMalloc(&ctx->counter, sizeof(unsigned long long));
     if (e != cudaSuccess) return bail(fail(ctx, RTPN_ENOMEM, "scratch allocation failed"));
+    e = cudaMalloc(&ctx->status, sizeof(unsigned));
+    if (e != cudaSuccess) return bail(fail(ctx, RTPN_ENOMEM, "status allocation failed"));
+    e = cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream);
+    if (e != cudaSuccess) return bail(fail(ctx, RTPN_ECUDA, cudaGetErrorString(e)));
     if ((rc = upload_tables(ctx))) return bail(rc);
     e = cudaMemsetAsync(ctx->u, 0, (size_t)ctx->md.nc * V * ctx->elem, ctx->stream);
     if (e != cudaSuccess) return bail(fail(ctx, RTPN_ECUDA, cudaGetErrorString(e)));
@@ -418,23 +453,31 @@ int rtpn_set_stream(rtpn_ctx* ctx, void* stream) {
 
 int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z) {
     if (!ctx) return RTPN_EINVAL;
-    if (kernel < RTPN_KERNEL_AUTO || kernel > RTPN_KERNEL_WINDOW)
+    if (kernel < RTPN_KERNEL_AUTO || kernel > RTPN_KERNEL_STAGE)
         return fail(ctx, RTPN_EINVAL, "unknown kernel");
     if (tile_x < 0 || tile_y < 0 || tile_z < 0) return fail(ctx, RTPN_EINVAL, "bad tile");
-    if (tile_x || tile_y || tile_z) {
+    if (kernel != RTPN_KERNEL_STAGE && (tile_x || tile_y || tile_z)) {
         const long long th = (long long)(tile_x ? tile_x : 32) * (tile_y ? tile_y : 4) *
                              (tile_z ? tile_z : 2);
         if (th > 256 || th % 32 != 0)
             return fail(ctx, RTPN_EINVAL, "tile must hold a multiple of 32 threads, at most 256");
     }
-    const int old = ctx->kernel;
+    const int old = ctx->kernel, ox = ctx->tx, oy = ctx->ty, oz = ctx->tz;
     ctx->kernel = kernel;
-    if (tile_x != ctx->tx || tile_y != ctx->ty || tile_z != ctx->tz) drop_graphs(ctx);
+    drop_graphs(ctx);
     ctx->tx = tile_x;
     ctx->ty = tile_y;
     ctx->tz = tile_z;
     int rc = choose_kernel(ctx);
-    if (rc) ctx->kernel = old;
+    if (rc) {
+        const std::string msg = ctx->err;
+        ctx->kernel = old;
+        ctx->tx = ox;
+        ctx->ty = oy;
+        ctx->tz = oz;
+        choose_kernel(ctx);
+        ctx->err = msg;
+    }
     return rc;
 }
 
@@ -443,8 +486,9 @@ int rtpn_set_media(rtpn_ctx* ctx, const void* sigma_a, const void* sigma_s, cons
     if (!ctx || !sigma_a || !sigma_s || !q) return RTPN_EINVAL;
     if (!valid_dtype(dtype) || !valid_where(where)) return fail(ctx, RTPN_EINVAL, "bad dtype/where");
     const long long V = ctx->g.V;
-    double* m = nullptr;
-    CUDA_TRY(ctx, cudaMalloc(&m, (size_t)3 * V * sizeof(double)));
+    // the FP64 media stay on the device (the adjoint needs them again)
+    if (!ctx->media) CUDA_TRY(ctx, cudaMalloc(&ctx->media, (size_t)3 * V * sizeof(double)));
+    double* m = ctx->media;
     const void* srcs[3] = {sigma_a, sigma_s, q};
     const size_t bytes = (size_t)V * dtype_size(dtype);
     int rc = RTPN_OK;
@@ -477,7 +521,6 @@ int rtpn_set_media(rtpn_ctx* ctx, const void* sigma_a, const void* sigma_s, cons
         if (e != cudaSuccess) rc = fail(ctx, RTPN_ECUDA, cudaGetErrorString(e));
     }
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    cudaFree(m);
     if (rc) return rc;
     if (e != cudaSuccess) return fail(ctx, RTPN_ECUDA, cudaGetErrorString(e));
     ctx->media_set = true;
@@ -589,6 +632,24 @@ int rtpn_count_nonfinite(rtpn_ctx* ctx, long long* out) {
 int rtpn_synchronize(rtpn_ctx* ctx) {
     if (!ctx) return RTPN_EINVAL;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    unsigned st = 0;
+    CUDA_TRY(ctx, cudaMemcpy(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st) {
+        CUDA_TRY(ctx, cudaMemset(ctx->status, 0, sizeof(unsigned)));
+        if (st & 1u) return fail(ctx, RTPN_ETIMEOUT, "a bounded wait in a staged kernel ran out");
+        return fail(ctx, RTPN_ECUDA, "a staged-kernel self-check failed (status " + std::to_string(st) + ")");
+    }
+    return RTPN_OK;
+}
+
+int rtpn_test_wait_timeout(rtpn_ctx* ctx, int cls, long long wait_limit) {
+    if (!ctx || cls < 0 || cls > 1 || wait_limit < 1) return RTPN_EINVAL;
+    if (ctx->active_kernel != RTPN_KERNEL_STAGE)
+        return fail(ctx, RTPN_EUNSUPPORTED, "the staged kernel is not active");
+    if (!ctx->media_set) return fail(ctx, RTPN_ESTATE, "rtpn_set_media has not been called");
+    // stage 1 of every CTA's sequence is never issued
+    int rc = launch_stage(ctx, cls, FAC_FULL, ctx->stream, 1, wait_limit);
+    if (rc) return fail(ctx, RTPN_ECUDA, cudaGetErrorString((cudaError_t)rc));
     return RTPN_OK;
 }
 

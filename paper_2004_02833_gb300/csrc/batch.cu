@@ -321,6 +321,7 @@ int rtpn_batch_create(rtpn_batch** out, int count, const int* N, const int* nx, 
         return RTPN_ENOMEM;
     }
     b->stream = b->own;
+    for (auto* c : b->ctx) rtpn_set_stream(c, b->own);
     int rc = build_items(b);
     if (rc) {
         release(b);

@@ -1,0 +1,170 @@
+// Host side of the TMA-staged kernels: variant registry, tensor maps, coupling tables, launch.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <vector>
+
+#include "stage_impl.cuh"
+#include "stage_variants.h"
+
+namespace rtpn {
+namespace stg {
+
+#define RTPN_SDECL(n, x, y, z)                                                                       \
+    int stage_launch_##n##_##x##_##y##_##z(int, int, const Args&, int, cudaStream_t);               \
+    int stage_smem_##n##_##x##_##y##_##z(int, int);
+RTPN_STAGE_VARIANTS(RTPN_SDECL)
+#undef RTPN_SDECL
+
+struct Variant {
+    int N, tx, ty, tz;
+    int (*launch)(int, int, const Args&, int, cudaStream_t);
+    int (*smem)(int, int);
+};
+#define RTPN_SENTRY(n, x, y, z) \
+    Variant{n, x, y, z, stage_launch_##n##_##x##_##y##_##z, stage_smem_##n##_##x##_##y##_##z},
+static const Variant kVariants[] = {RTPN_STAGE_VARIANTS(RTPN_SENTRY)};
+#undef RTPN_SENTRY
+
+static const Variant* find(int N, int tx, int ty, int tz) {
+    for (const auto& v : kVariants)
+        if (v.N == N && (tx == 0 || (v.tx == tx && v.ty == ty && v.tz == tz))) return &v;
+    return nullptr;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+static bool make_map(CUtensorMap* m, void* base, int precision, const rtpn::Geom& g, int nc, int bx, int by,
+                     int bz) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t es = precision == RTPN_BF16 ? 2 : 4;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)nc};
+    const cuuint64_t strides[3] = {g.nx * es, (cuuint64_t)g.nx * g.ny * es, (cuuint64_t)g.V * es};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = fn(m, precision == RTPN_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace stg
+
+bool stage_supported(int N, int precision, int nx) {
+    if (precision == RTPN_FP64 || !stg::find(N, 0, 0, 0)) return false;
+    const int hx = precision == RTPN_BF16 ? 8 : 4;  // 16-byte rows for the tensor maps
+    return nx % hx == 0;
+}
+
+bool stage_has_tile(int N, int tx, int ty, int tz) { return stg::find(N, tx, ty, tz) != nullptr; }
+
+int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz) {
+    const stg::Variant* v = stg::find(ctx->N, tx, ty, tz);
+    if (!v) return (int)cudaErrorNotSupported;
+    // the wider default tile when it divides nx exactly
+    if (tx == 0)
+        for (const auto& w : stg::kVariants)
+            if (w.N == ctx->N && ctx->g.nx % w.tx == 0 && w.tx > v->tx) v = &w;
+    const int es = ctx->prec == RTPN_BF16 ? 2 : 4;
+    const int hx = 16 / es;
+    // the four tensor maps live in device global memory (64-byte aligned) and the kernel reads
+    // them from there: tile box, x-halo group, y-halo row, z-halo plane
+    alignas(64) CUtensorMap maps[4];
+    if (!stg::make_map(&maps[0], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, v->tz) ||
+        !stg::make_map(&maps[1], ctx->u, ctx->prec, ctx->g, ctx->md.nc, hx, v->ty, v->tz) ||
+        !stg::make_map(&maps[2], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, 1, v->tz) ||
+        !stg::make_map(&maps[3], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, 1))
+        return (int)cudaErrorInvalidValue;
+    if (!ctx->stage_maps_dev) {
+        cudaError_t e = cudaMalloc(&ctx->stage_maps_dev, sizeof(maps));
+        if (e != cudaSuccess) return (int)e;
+    }
+    {
+        cudaError_t e = cudaMemcpy(ctx->stage_maps_dev, maps, sizeof(maps), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return (int)e;
+    }
+    if (!ctx->stage_mem) {
+        // coupling tables of both classes (CPAD floats per source) and the column starts
+        const int N = ctx->N;
+        std::vector<float> tab[2];
+        for (int A = 0; A < 2; ++A) {
+            std::vector<float> t10;
+            if (!win::coef_table(ctx->md, A, &t10)) return (int)cudaErrorInvalidValue;
+            const size_t ns = t10.size() / 10;
+            tab[A].assign(ns * stg::CPAD, 0.f);
+            for (size_t j = 0; j < ns; ++j)
+                for (int k = 0; k < 10; ++k) tab[A][j * stg::CPAD + k] = t10[j * 10 + k];
+        }
+        std::vector<int> col(2 * (N + 2));
+        for (int P = 0; P < 2; ++P) {
+            int acc = 0;
+            for (int M = 0; M <= N + 1; ++M) {
+                col[P * (N + 2) + M] = acc;
+                if (M <= N) acc += win::ntypes(M) * win::column_len(N, M, P);
+            }
+        }
+        const size_t b0 = tab[0].size() * 4, b1 = tab[1].size() * 4, b2 = col.size() * 4;
+        cudaError_t e = cudaMalloc(&ctx->stage_mem, b0 + b1 + b2);
+        if (e != cudaSuccess) return (int)e;
+        char* m = (char*)ctx->stage_mem;
+        cudaMemcpy(m, tab[0].data(), b0, cudaMemcpyHostToDevice);
+        cudaMemcpy(m + b0, tab[1].data(), b1, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(m + b0 + b1, col.data(), b2, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return (int)e;
+        ctx->stage_tab_bytes[0] = b0;
+        ctx->stage_tab_bytes[1] = b1;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+    ctx->stage_variant = (int)(v - stg::kVariants);
+    ctx->tx = v->tx;
+    ctx->ty = v->ty;
+    ctx->tz = v->tz;
+    return 0;
+}
+
+int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long skip_stage,
+                 long long wait_limit) {
+    if (ctx->stage_variant < 0) return (int)cudaErrorNotSupported;
+    const stg::Variant& v = stg::kVariants[ctx->stage_variant];
+    stg::Args a;
+    a.u = ctx->u;
+    a.fac = (const float*)ctx->fac;
+    // class cls's targets read the coefficients of the other class's sources (table A = cls)
+    const char* m = (const char*)ctx->stage_mem;
+    a.coef = (const float*)(cls == 0 ? m : m + ctx->stage_tab_bytes[0]);
+    a.colstart = (const int*)(m + ctx->stage_tab_bytes[0] + ctx->stage_tab_bytes[1]);
+    a.V = ctx->g.V;
+    a.nx = ctx->g.nx;
+    a.ny = ctx->g.ny;
+    a.nz = ctx->g.nz;
+    a.bc = ctx->g.bc;
+    a.fac_ofs = fac_ofs;
+    a.inv_h = (float)(1.0 / ctx->g.h);
+    a.ntx = (a.nx + v.tx - 1) / v.tx;
+    a.nty = (a.ny + v.ty - 1) / v.ty;
+    a.ntz = (a.nz + v.tz - 1) / v.tz;
+    a.tiles = (long long)a.ntx * a.nty * a.ntz;
+    a.maps = (const CUtensorMap*)ctx->stage_maps_dev;
+    a.nc = ctx->md.nc;
+    a.status = ctx->status;
+    a.wait_limit = wait_limit;
+    a.skip_stage = skip_stage;
+    return v.launch(cls, ctx->prec, a, ctx->sms, st);
+}
+
+}  // namespace rtpn

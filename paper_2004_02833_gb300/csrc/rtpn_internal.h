@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <map>
 #include <string>
 #include <vector>
@@ -79,6 +80,19 @@ bool window_supported(int N, int precision);
 int window_prepare(const Model& md, double h, int precision);
 int launch_window(int N, int precision, const WindowLaunch& w, cudaStream_t st);
 
+// transposed partner table (adjoint.cu): targets of class clsB, sources of the other class
+HostTable transposed_table(const Model& md, int clsB, double h);
+
+// ---- TMA-staged kernels (kernels_stage.cu, stage.cu) ----
+// nx must give 16-byte rows for the tensor maps
+bool stage_supported(int N, int precision, int nx);
+bool stage_has_tile(int N, int tx, int ty, int tz);
+// builds the tensor maps (tile 0,0,0 = default) and the coupling tables; returns cudaError_t
+int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz);
+int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long skip_stage,
+                 long long wait_limit);
+constexpr long long STAGE_WAIT_LIMIT = 1ll << 22;  // mbarrier polls before a wait gives up
+
 }  // namespace rtpn
 
 struct rtpn_ctx {
@@ -96,11 +110,16 @@ struct rtpn_ctx {
     double* partial = nullptr;       // reduction partials [SUM_BLOCKS] + result
     unsigned long long* counter = nullptr;
     void* staging = nullptr;         // one plane of FP64 (conversions, media upload)
-    double* media = nullptr;         // 3 planes of FP64 media during set_media
+    double* media = nullptr;         // FP64 sigma_a, sigma_s, q as last set (3 planes)
     cudaStream_t stream = nullptr;   // work stream (user's or own)
     cudaStream_t own = nullptr;      // private stream (capture, default work stream)
     bool media_set = false;
     long long steps_done = 0;
     std::map<int, cudaGraphExec_t> graphs;  // pair-sequence graphs keyed by pair count
     std::string err;
+    unsigned* status = nullptr;      // device status word of bounded waits (0 = fine)
+    void* stage_mem = nullptr;       // staged kernels: coupling tables of both classes + column starts
+    size_t stage_tab_bytes[2] = {0, 0};
+    int stage_variant = -1, sms = 0;
+    void* stage_maps_dev = nullptr;  // four CUtensorMap of the staged kernel (device global memory)
 };

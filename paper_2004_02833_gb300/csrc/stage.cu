@@ -1,0 +1,63 @@
+// One variant of the TMA-staged substep kernel: order RTPN_SN, CTA tile RTPN_STX x RTPN_STY x
+// RTPN_STZ, both target classes, FP32 and BF16 storage.  kernels_stage.cu dispatches to it.
+#include "stage_impl.cuh"
+
+#if !defined(RTPN_SN) || !defined(RTPN_STX) || !defined(RTPN_STY) || !defined(RTPN_STZ)
+#error "compile with -DRTPN_SN=<order> -DRTPN_STX=.. -DRTPN_STY=.. -DRTPN_STZ=.."
+#endif
+
+#define RTPN_SCAT2(a, b, c, d, e) a##_##b##_##c##_##d##_##e
+#define RTPN_SCAT(a, b, c, d, e) RTPN_SCAT2(a, b, c, d, e)
+#define RTPN_SVARIANT(name) RTPN_SCAT(name, RTPN_SN, RTPN_STX, RTPN_STY, RTPN_STZ)
+
+namespace rtpn {
+namespace stg {
+
+constexpr int kN = RTPN_SN, kTX = RTPN_STX, kTY = RTPN_STY, kTZ = RTPN_STZ;
+
+template <int A, typename S>
+__global__ void __launch_bounds__(kTX * kTY * kTZ, 1) k_stage(Args a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    stage_kernel_body<kN, A, S, kTX, kTY, kTZ>(a, smem);
+}
+
+template <int A, typename S>
+int launch_one(const Args& a, int sms, cudaStream_t st) {
+    using L = Layout<kN, A, S, kTX, kTY, kTZ>;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_stage<A, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             L::BYTES);
+        if (e != cudaSuccess) return (int)e;
+        configured[dev] = true;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<A, S>,
+                                                                  kTX * kTY * kTZ, L::BYTES);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorLaunchOutOfResources;
+    long long grid = (long long)per_sm * sms;
+    if (grid > a.tiles) grid = a.tiles;
+    if (grid < 1) return 0;
+    k_stage<A, S><<<(unsigned)grid, kTX * kTY * kTZ, L::BYTES, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+int RTPN_SVARIANT(stage_launch)(int cls, int precision, const Args& a, int sms, cudaStream_t st) {
+    if (precision == RTPN_BF16)
+        return cls == 0 ? launch_one<0, __nv_bfloat16>(a, sms, st) : launch_one<1, __nv_bfloat16>(a, sms, st);
+    return cls == 0 ? launch_one<0, float>(a, sms, st) : launch_one<1, float>(a, sms, st);
+}
+
+int RTPN_SVARIANT(stage_smem)(int cls, int precision) {
+    if (precision == RTPN_BF16)
+        return cls == 0 ? Layout<kN, 0, __nv_bfloat16, kTX, kTY, kTZ>::BYTES
+                        : Layout<kN, 1, __nv_bfloat16, kTX, kTY, kTZ>::BYTES;
+    return cls == 0 ? Layout<kN, 0, float, kTX, kTY, kTZ>::BYTES : Layout<kN, 1, float, kTX, kTY, kTZ>::BYTES;
+}
+
+}  // namespace stg
+}  // namespace rtpn

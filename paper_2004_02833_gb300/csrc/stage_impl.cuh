@@ -1,0 +1,446 @@
+// TMA-staged substep kernel with a compact column loop (FP32 arithmetic, FP32 or BF16 storage).
+//
+// Arithmetic as in the register-window kernel (window_impl.cuh): one thread per cell of a CTA tile
+// sweeps the frozen class column by column in |m| and scatters three half-grid differences per
+// source into the accumulators of its <= 10 targets (Eqs. 4-5; Section 3.2's unrolled sparse
+// product), a target column being finished once the next source column is in.  Two things differ:
+//
+//  * The column sweep is a runtime loop whose body handles one column for every (type, l) slot of
+//    the class; the three live target columns are three register arrays that shift by one column
+//    per iteration.  Slots that do not exist in a column are skipped (sources) or carry zero
+//    coefficients (targets), so the body is the same for every column and stays small enough for
+//    the instruction cache (the fully unrolled body of the register-window kernel is not).
+//  * The data of a column reach shared memory through the Tensor Memory Accelerator
+//    (cp.async.bulk.tensor), double buffered: while column M is computed the copies of column M+1
+//    are in flight.  A column stage holds, per source component, the tile box plus one halo slab on
+//    the side its partners read along each axis (x: an aligned 16-byte group, y: one row, z: one
+//    plane), and, per target component of the column being finished, its tile box.  Periodic halos
+//    use wrapped coordinates; vacuum halos use out-of-range coordinates, which the TMA unit fills
+//    with zeros.  The coupling constants sit in shared memory.
+//
+// CTAs are persistent (one per SM) and walk tiles in z-fastest order; the stage sequence runs on
+// across tiles so the pipeline never drains.  Every mbarrier wait is bounded: one that runs out
+// sets a status bit, and the CTA leaves after a second bounded wait for the copies in flight.
+#pragma once
+
+#include <cuda.h>
+
+#include "window_impl.cuh"
+
+namespace rtpn {
+namespace stg {
+
+using win::class_size;
+using win::column_len;
+using win::first_l;
+using win::ntypes;
+using win::static_for;
+
+constexpr unsigned STATUS_TIMEOUT = 1u;
+constexpr unsigned STATUS_CHECK = 2u;  // a self-check failed (builds with RTPN_STAGE_CHECKS)
+constexpr int CPAD = 12;  // coefficients per source in shared memory (10 used), three float4
+
+struct Args {
+    void* u;
+    const float* fac;
+    const float* coef;      // [class-B source][CPAD] in global memory (copied to shared memory)
+    const int* colstart;    // [2][N+2]: first local index of column M in class 0 / class 1
+    long long V;
+    int nx, ny, nz, bc;
+    int fac_ofs;
+    float inv_h;
+    int ntx, nty, ntz;
+    long long tiles;
+    const CUtensorMap* maps;  // four tensor maps in global memory: tile, x halo, y halo, z halo
+    int nc;                   // components (bound of the 4th tensor coordinate)
+    unsigned* status;       // device status word (STATUS_TIMEOUT on a wait that ran out)
+    long long wait_limit;   // try_wait polls before giving up
+    long long skip_stage;   // global stage index never issued (a wait that must run out); -1 normally
+};
+
+__host__ __device__ constexpr int pad128(int bytes) { return (bytes + 127) / 128 * 128; }
+
+template <int N, int A, typename S, int TX, int TY, int TZ>
+struct Layout {
+    static constexpr int B = 1 - A;
+    static constexpr int NL = N / 2 + 1;
+    static constexpr int SLOTS = 2 * NL;  // (type, l/2) slots of a column
+    static constexpr int ES = (int)sizeof(S);
+    static constexpr int HX = 16 / ES;    // x halo: one aligned 16-byte group
+    static constexpr int CTR_BYTES = TX * TY * TZ * ES;
+    static constexpr int HX_BYTES = HX * TY * TZ * ES;
+    static constexpr int HY_BYTES = TX * TZ * ES;
+    static constexpr int HZ_BYTES = TX * TY * ES;
+    static constexpr int CTR = pad128(CTR_BYTES);
+    static constexpr int HXO = CTR;                        // offsets inside a source slot
+    static constexpr int HYO = HXO + pad128(HX_BYTES);
+    static constexpr int HZO = HYO + pad128(HY_BYTES);
+    static constexpr int SRC = HZO + pad128(HZ_BYTES);
+    static constexpr int SRC_TX = CTR_BYTES + HX_BYTES + HY_BYTES + HZ_BYTES;  // bytes per source
+    static constexpr int TGT0 = SLOTS * SRC;               // target slots after the source slots
+    static constexpr int BUF = TGT0 + SLOTS * CTR;
+    static constexpr int COEF = pad128(class_size(N, B) * CPAD * 4);
+    static constexpr int BYTES = COEF + 2 * BUF + 128;     // table, two buffers, mbarriers
+    static_assert(TX % HX == 0, "tile width must be a multiple of the 16-byte group");
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int x, int y, int z,
+                                            int c, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(c), "r"(bar)
+        : "memory");
+}
+// bounded wait on one mbarrier phase; false if it ran out
+__device__ __forceinline__ bool wait_phase(unsigned bar, unsigned parity, long long limit) {
+    for (long long i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <typename S>
+__device__ __forceinline__ float lds(const unsigned char* base, int byte_off) {
+    if constexpr (sizeof(S) == 4) {
+        return *reinterpret_cast<const float*>(base + byte_off);
+    } else {
+        return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(base + byte_off));
+    }
+}
+
+// Optional self-checks (compile with -DRTPN_STAGE_CHECKS): an index or alignment that breaks the
+// layout sets STATUS_CHECK and the access is skipped.
+#ifdef RTPN_STAGE_CHECKS
+#define RTPN_SCHECK(cond) ((cond) ? true : (atomicOr(a.status, STATUS_CHECK), false))
+#else
+#define RTPN_SCHECK(cond) true
+#endif
+
+// Tile geometry: origin, valid extents and halo coordinates ([axis][side], side 1 = upper).
+struct TileGeo {
+    int x0, y0, z0, wx, wy, wz;
+    int hc[3][2];
+    int hx_start[2], hx_elem[2];
+};
+
+template <int TX, int TY, int TZ, int HX>
+__device__ __forceinline__ TileGeo tile_geo(const Args& a, long long t) {
+    TileGeo g;
+    const long long bz = t % a.ntz;
+    const long long rest = t / a.ntz;
+    g.x0 = (int)(rest % a.ntx) * TX;
+    g.y0 = (int)(rest / a.ntx) * TY;
+    g.z0 = (int)bz * TZ;
+    g.wx = min(TX, a.nx - g.x0);
+    g.wy = min(TY, a.ny - g.y0);
+    g.wz = min(TZ, a.nz - g.z0);
+    const bool periodic = a.bc == RTPN_BC_PERIODIC;
+    const int o[3] = {g.x0, g.y0, g.z0}, w[3] = {g.wx, g.wy, g.wz}, n[3] = {a.nx, a.ny, a.nz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int up = o[d] + w[d], lo = o[d] - 1;
+        if (periodic) {
+            if (up >= n[d]) up -= n[d];
+            if (lo < 0) lo += n[d];
+        }
+        g.hc[d][1] = up;
+        g.hc[d][0] = lo;
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int xn = g.hc[0][s];
+        const int st = xn >= 0 ? (xn / HX) * HX : -HX;
+        g.hx_start[s] = st;
+        g.hx_elem[s] = xn - st;
+    }
+    return g;
+}
+
+// Source x slot: 1 (read at i+1 by its partners) iff (M even) == (cos type); z slot: 1 iff l+M even.
+__device__ __forceinline__ int dir_x(int M, int t) { return ((M & 1) == 0) == (t == 0) ? 1 : -1; }
+
+template <int N, int A, typename S, int TX, int TY, int TZ>
+__device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* smem) {
+    using L = Layout<N, A, S, TX, TY, TZ>;
+    constexpr int B = 1 - A;
+    constexpr int NL = L::NL;
+    constexpr int HX = L::HX;
+    constexpr int NSTAGE = N + 2;  // stage i: sources of column i (i <= N), targets of column i-1
+    const int cA0 = A == 0 ? 0 : class_size(N, 0);
+    const int cB0 = B == 0 ? 0 : class_size(N, 0);
+    const int* colA = a.colstart + A * (N + 2);
+    const int* colB = a.colstart + B * (N + 2);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+    const long long V = a.V;
+
+    float* coef = reinterpret_cast<float*>(smem);
+    unsigned char* bufs = smem + L::COEF;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(bufs + 2 * L::BUF);
+    const unsigned bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+
+    const CUtensorMap* map_ctr = a.maps;
+    const CUtensorMap* map_hx = a.maps + 1;
+    const CUtensorMap* map_hy = a.maps + 2;
+    const CUtensorMap* map_hz = a.maps + 3;
+
+    // coupling constants into shared memory
+    for (int i = tid; i < class_size(N, B) * CPAD; i += TX * TY * TZ) coef[i] = a.coef[i];
+    if (tid < 4) {
+        // the maps were written by the host before the launch; make them visible to the async proxy
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(a.maps + tid)
+                     : "memory");
+    }
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    const long long my_tiles = a.tiles > blockIdx.x ? (a.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long total = my_tiles * NSTAGE;
+
+    // Issue global stage s (tile s / NSTAGE of this CTA, column stage s % NSTAGE): warp 0.
+    auto issue = [&](long long s) {
+        if (s == a.skip_stage) return;
+        const long long ti = blockIdx.x + (s / NSTAGE) * (long long)gridDim.x;
+        const int i = (int)(s % NSTAGE);
+        const TileGeo g = tile_geo<TX, TY, TZ, HX>(a, ti);
+        unsigned char* buf = bufs + (s & 1) * L::BUF;
+        const unsigned bar = (s & 1) ? bar1 : bar0;
+        const int nsrc = i <= N ? ntypes(i) * column_len(N, i, B) : 0;
+        const int ntgt = i >= 1 ? ntypes(i - 1) * column_len(N, i - 1, A) : 0;
+        if (lane == 0) mbar_expect_tx(bar, nsrc * L::SRC_TX + ntgt * L::CTR_BYTES);
+        __syncwarp();
+        for (int j = lane; j < 2 * L::SLOTS; j += 32) {
+            if (j < L::SLOTS) {  // source slot j = t * NL + l/2 of column i
+                const int t = j / NL, l = 2 * (j % NL) + B;
+                if (i > N || l < i || l > N || (t == 1 && i == 0)) continue;
+                const int c = cB0 + colB[i] + t * column_len(N, i, B) + (l - first_l(i, B)) / 2;
+                const unsigned d = smem_addr(buf + j * L::SRC);
+                const int sx = dir_x(i, t) > 0 ? 1 : 0;
+                const int sy = t == 0 ? 1 : 0;
+                const int sz = ((l + i) & 1) == 0 ? 1 : 0;
+                const int hxs = sx ? g.hx_start[1] : g.hx_start[0];
+                if (!RTPN_SCHECK(c >= 0 && c < a.nc && g.x0 % HX == 0 && hxs % HX == 0 &&
+                                 j * L::SRC + L::SRC <= L::TGT0 && (d & 127) == 0))
+                    continue;
+                tma_load_4d(d, map_ctr, g.x0, g.y0, g.z0, c, bar);
+                tma_load_4d(d + L::HXO, map_hx, hxs, g.y0, g.z0, c, bar);
+                tma_load_4d(d + L::HYO, map_hy, g.x0, sy ? g.hc[1][1] : g.hc[1][0], g.z0, c, bar);
+                tma_load_4d(d + L::HZO, map_hz, g.x0, g.y0, sz ? g.hc[2][1] : g.hc[2][0], c, bar);
+            } else {  // target slot of column i - 1
+                const int jj = j - L::SLOTS;
+                const int M = i - 1;
+                const int t = jj / NL, l = 2 * (jj % NL) + A;
+                if (M < 0 || l < M || l > N || (t == 1 && M == 0)) continue;
+                const int c = cA0 + colA[M] + t * column_len(N, M, A) + (l - first_l(M, A)) / 2;
+                const unsigned d = smem_addr(buf + L::TGT0 + jj * L::CTR);
+                if (!RTPN_SCHECK(c >= 0 && c < a.nc && g.x0 % HX == 0 &&
+                                 L::TGT0 + jj * L::CTR + L::CTR <= L::BUF && (d & 127) == 0))
+                    continue;
+                tma_load_4d(d, map_ctr, g.x0, g.y0, g.z0, c, bar);
+            }
+        }
+    };
+
+    float prev[2][NL], cur[2][NL], next[2][NL];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int q = 0; q < NL; ++q) prev[t][q] = cur[t][q] = next[t][q] = 0.f;
+
+    if (tid < 32 && total > 0) issue(0);
+    long long fail_at = -1;
+
+    TileGeo g{};
+    bool active = false;
+    long long cell = 0;
+    float al[8], be[8];
+    float al0 = 0.f, be0 = 0.f, ga0 = 0.f;
+    int my = 0, offy[2] = {0, 0};
+
+    for (long long s = 0; s < total; ++s) {
+        const int i = (int)(s % NSTAGE);
+        if (i == 0) {  // new tile: geometry, factors, fixed neighbour offsets
+            g = tile_geo<TX, TY, TZ, HX>(a, blockIdx.x + (s / NSTAGE) * (long long)gridDim.x);
+            active = lx < g.wx && ly < g.wy && lz < g.wz;
+            cell = ((long long)(g.z0 + lz) * a.ny + (g.y0 + ly)) * a.nx + (g.x0 + lx);
+            my = ((lz * TY + ly) * TX + lx) * L::ES;
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {  // y slot is fixed per type: cos reads y+1, sin y-1
+                const int dy = t == 0 ? 1 : -1;
+                offy[t] = (ly + dy >= 0 && ly + dy < g.wy) ? my + dy * TX * L::ES
+                                                         : L::HYO + (lz * TX + lx) * L::ES;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) al[k] = be[k] = 0.f;
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int twos = (k & 1) + ((k >> 1) & 1) + ((k >> 2) & 1);
+                    if (twos % 2 == A) {
+                        al[k] = __ldg(a.fac + (long long)(a.fac_ofs + 2 * k) * V + cell);
+                        be[k] = __ldg(a.fac + (long long)(a.fac_ofs + 2 * k + 1) * V + cell) * a.inv_h;
+                    }
+                }
+                if (A == 0) {
+                    al0 = __ldg(a.fac + (long long)FAC_U0 * V + cell);
+                    be0 = __ldg(a.fac + (long long)(FAC_U0 + 1) * V + cell) * a.inv_h;
+                    ga0 = __ldg(a.fac + (long long)(FAC_U0 + 2) * V + cell);
+                }
+            }
+        }
+        const unsigned bar = (s & 1) ? bar1 : bar0;
+        const bool ok = wait_phase(bar, (unsigned)((s >> 1) & 1), a.wait_limit);
+        if (__syncthreads_or(!ok)) {
+            fail_at = s;
+            break;
+        }
+        if (tid < 32 && s + 1 < total) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(s + 1);
+        }
+        const unsigned char* buf = bufs + (s & 1) * L::BUF;
+
+        if (active && i <= N) {
+            // ---- scatter source column i into prev (i-1), cur (i), next (i+1)
+            const int Ms = i;
+            const int dz = ((B + Ms) & 1) == 0 ? 1 : -1;
+            const int offz = (lz + dz >= 0 && lz + dz < g.wz) ? my + dz * TX * TY * L::ES
+                                                              : L::HZO + (ly * TX + lx) * L::ES;
+            static_for<2>([&](auto ti) {
+                constexpr int ts = decltype(ti)::value;
+                if (ts == 1 && Ms == 0) return;
+                const int dx = dir_x(Ms, ts);
+                const int offx = (lx + dx >= 0 && lx + dx < g.wx)
+                                     ? my + dx * L::ES
+                                     : L::HXO + ((lz * TY + ly) * HX + (dx > 0 ? g.hx_elem[1] : g.hx_elem[0])) * L::ES;
+                // local index of slot (ts, q) is cbase + q
+                const int cbase = colB[Ms] + ts * column_len(N, Ms, B) - first_l(Ms, B) / 2;
+                static_for<NL>([&](auto qi) {
+                    constexpr int q = decltype(qi)::value;
+                    constexpr int ls = 2 * q + B;
+                    if constexpr (ls <= N) {
+                        if (ls < Ms) return;
+                        const unsigned char* base = buf + (ts * NL + q) * L::SRC;
+                        if (!RTPN_SCHECK(offx >= 0 && offx < L::SRC && offy[ts] >= 0 && offy[ts] < L::SRC &&
+                                         offz >= 0 && offz < L::SRC && my < L::CTR_BYTES &&
+                                         cbase + q >= 0 && cbase + q < class_size(N, B)))
+                            return;
+                        const float c = lds<S>(base, my);
+                        const float ddx = lds<S>(base, offx) - c;
+                        const float ddy = lds<S>(base, offy[ts]) - c;
+                        const float ddz = lds<S>(base, offz) - c;
+                        const float4* cf = reinterpret_cast<const float4*>(coef + (cbase + q) * CPAD);
+                        const float4 k0 = cf[0], k1 = cf[1], k2 = cf[2];
+                        constexpr int lm = (ls - 1) / 2, lp = (ls + 1) / 2;  // acc index of l-1, l+1
+                        constexpr bool has_m = ls - 1 >= 0, has_p = ls + 1 <= N;
+                        if constexpr (has_m) cur[ts][lm] = fmaf(k0.x, ddz, cur[ts][lm]);
+                        if constexpr (has_p) cur[ts][lp] = fmaf(k0.y, ddz, cur[ts][lp]);
+                        if constexpr (has_m) prev[ts][lm] = fmaf(k0.z, ddx, prev[ts][lm]);
+                        if constexpr (has_p) prev[ts][lp] = fmaf(k0.w, ddx, prev[ts][lp]);
+                        if constexpr (has_m) next[ts][lm] = fmaf(k1.x, ddx, next[ts][lm]);
+                        if constexpr (has_p) next[ts][lp] = fmaf(k1.y, ddx, next[ts][lp]);
+                        if constexpr (has_m) prev[1 - ts][lm] = fmaf(k1.z, ddy, prev[1 - ts][lm]);
+                        if constexpr (has_p) prev[1 - ts][lp] = fmaf(k1.w, ddy, prev[1 - ts][lp]);
+                        if constexpr (has_m) next[1 - ts][lm] = fmaf(k2.x, ddy, next[1 - ts][lm]);
+                        if constexpr (has_p) next[1 - ts][lp] = fmaf(k2.y, ddy, next[1 - ts][lp]);
+                    }
+                });
+            });
+        }
+        if (active && i >= 1) {
+            // ---- finish target column i - 1 (its accumulators are in prev)
+            const int M = i - 1;
+            static_for<2>([&](auto ti) {
+                constexpr int t = decltype(ti)::value;
+                if (t == 1 && M == 0) return;
+                // slot of (l, M, t) for l of class A: x by (M, t), y by t, z by (A + M)
+                const int gx = (((M & 1) == 0) == (t == 0)) ? 0 : 1;
+                const int gz = ((A + M) & 1) == 0 ? 0 : 1;
+                const int gcode = gx + 2 * t + 4 * gz;
+                float alpha = 0.f, beta = 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (k == gcode) {
+                        alpha = al[k];
+                        beta = be[k];
+                    }
+                S* tptr = reinterpret_cast<S*>(a.u) +
+                          (long long)(cA0 + colA[M] + t * column_len(N, M, A) - first_l(M, A) / 2) * V +
+                          cell;
+                static_for<NL>([&](auto qi) {
+                    constexpr int q = decltype(qi)::value;
+                    constexpr int l = 2 * q + A;
+                    if constexpr (l <= N) {
+                        if (l < M) return;
+                        const long long gi = (long long)(cA0 + colA[M] + t * column_len(N, M, A) -
+                                                         first_l(M, A) / 2 + q);
+                        if (!RTPN_SCHECK(gi >= cA0 && gi < a.nc && cell >= 0 && cell < V)) return;
+                        const float old = lds<S>(buf + L::TGT0 + (t * NL + q) * L::CTR, my);
+                        const float r = prev[t][q];
+                        float nv;
+                        if (A == 0 && l == 0 && M == 0)
+                            nv = fmaf(al0, old, fmaf(-be0, r, ga0));
+                        else
+                            nv = fmaf(alpha, old, -beta * r);
+                        win::store<S>(tptr + (long long)q * V, nv);
+                    }
+                });
+            });
+        }
+        // shift the window: prev <- cur <- next <- 0 (also resets a finished tile)
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                prev[t][q] = cur[t][q];
+                cur[t][q] = next[t][q];
+                next[t][q] = 0.f;
+            }
+        if (i == NSTAGE - 1) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int q = 0; q < NL; ++q) prev[t][q] = cur[t][q] = 0.f;
+        }
+        __syncthreads();  // buffer s & 1 may be refilled by stage s + 2
+    }
+
+    if (fail_at >= 0) {
+        if (tid == 0) atomicOr(a.status, STATUS_TIMEOUT);
+        // Only the copies of the stage that timed out can still be in flight (the next stage is
+        // issued after a successful wait); give them one more bounded wait before leaving.
+        wait_phase((fail_at & 1) ? bar1 : bar0, (unsigned)((fail_at >> 1) & 1), a.wait_limit);
+        __syncthreads();
+    }
+}
+
+}  // namespace stg
+}  // namespace rtpn

@@ -18,7 +18,7 @@ BC = {"periodic": 0, "vacuum": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 DTYPE_F64, DTYPE_F32 = 0, 1
 HOST, DEVICE = 0, 1
-KERNEL = {"auto": 0, "generic": 1, "window": 2}
+KERNEL = {"auto": 0, "generic": 1, "window": 2, "stage": 3}
 
 
 class RtpnError(RuntimeError):
@@ -63,6 +63,21 @@ SIGNATURES = {
     "rtpn_count_nonfinite": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "rtpn_sum_static": (_I, [_P, _I, ctypes.c_longlong, _P, _P]),
     "rtpn_synchronize": (_I, [_P]),
+    "rtpn_test_wait_timeout": (_I, [_P, _I, ctypes.c_longlong]),
+    "rtpn_adjoint": (_I, [_P, _P, _I, _I, _I, _I, _P, _P, _P, _I, ctypes.POINTER(_D)]),
+    "rtpn_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _P, _P, _I]),
+    "rtpn_batch_destroy": (_I, [_P]),
+    "rtpn_batch_count": (_I, [_P]),
+    "rtpn_batch_instance": (_P, [_P, _I]),
+    "rtpn_batch_set_stream": (_I, [_P, _P]),
+    "rtpn_batch_set_tile": (_I, [_P, _I, _I, _I]),
+    "rtpn_batch_get_tile": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "rtpn_batch_step": (_I, [_P, _I]),
+    "rtpn_batch_step_looped": (_I, [_P, _I]),
+    "rtpn_batch_synchronize": (_I, [_P]),
+    "rtpn_batch_last_error": (ctypes.c_char_p, [_P]),
+    "rtpn_autotune": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "rtpn_batch_autotune": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "rtpn_get_info": (_I, [_P, ctypes.POINTER(Info)]),
     "rtpn_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -190,6 +205,13 @@ class Context:
     def set_kernel(self, kernel: str = "auto", tile=(0, 0, 0)):
         self._chk(lib().rtpn_set_kernel(self._p, KERNEL[kernel], *tile))
 
+    def autotune(self, reps: int = 2):
+        """Time candidate window-kernel tiles on this context's data, apply the best; (tile, ms)."""
+        tile = (_I * 3)()
+        ms = _D()
+        self._chk(lib().rtpn_autotune(self._p, int(reps), tile, ctypes.byref(ms)))
+        return tuple(tile), ms.value
+
     def info(self) -> Info:
         out = Info()
         self._chk(lib().rtpn_get_info(self._p, ctypes.byref(out)))
@@ -241,6 +263,25 @@ class Context:
 
     _pass = substep
 
+    def adjoint(self, w, k: int, ckpt_every: int = 20, out=None):
+        """J = sum w u_0 after k steps from the current state, and dJ/d(sigma_a, sigma_s, q) per
+        cell (FP64).  `out`: optional tuple of three float64 tensors/arrays to fill (host or CUDA);
+        otherwise numpy arrays are returned.  The context then holds the state after k steps."""
+        ptr, code, where, keep = _buf(w)
+        if out is None:
+            out = tuple(np.empty(self.shape, dtype=np.float64) for _ in range(3))
+        bufs = [_buf(o) for o in out]
+        for b in bufs:
+            if b[1] != DTYPE_F64:
+                raise TypeError("gradient buffers must be float64")
+        ow = {b[2] for b in bufs}
+        if len(ow) != 1:
+            raise ValueError("gradient buffers must share the memory kind")
+        J = _D()
+        self._chk(lib().rtpn_adjoint(self._p, ptr, code, where, int(k), int(ckpt_every), bufs[0][0],
+                                     bufs[1][0], bufs[2][0], ow.pop(), ctypes.byref(J)))
+        return J.value, out
+
     def sum_u0(self) -> float:
         out = _D()
         self._chk(lib().rtpn_sum_u0(self._p, ctypes.byref(out)))
@@ -255,3 +296,99 @@ class Context:
 
     def synchronize(self):
         self._chk(lib().rtpn_synchronize(self._p))
+
+
+class _Instance(Context):
+    """A batch member: the context is owned by the batch (never destroyed here)."""
+
+    def __init__(self, ptr, N, shape, h, bc, precision):
+        self._p = _P(ptr)
+        self.N, self.shape, self.h, self.bc, self.precision = N, tuple(shape), h, bc, precision
+        self.n_c = (N + 1) ** 2
+
+    def close(self):
+        self._p = None
+
+
+class Batch:
+    """Independent instances advanced together by one grouped launch per pass."""
+
+    def __init__(self, instances, precision: str = "fp32"):
+        """instances: iterable of (N, (nz, ny, nx), h, bc, dt or None)."""
+        inst = list(instances)
+        n = len(inst)
+        arr_i = lambda vals: (_I * n)(*vals)
+        arr_d = lambda vals: (_D * n)(*vals)
+        Ns = arr_i([i[0] for i in inst])
+        nz = arr_i([i[1][0] for i in inst])
+        ny = arr_i([i[1][1] for i in inst])
+        nx = arr_i([i[1][2] for i in inst])
+        hs = arr_d([i[2] for i in inst])
+        bcs = arr_i([BC[i[3]] for i in inst])
+        dts = arr_d([float(i[4] or 0.0) for i in inst])
+        p = _P()
+        rc = lib().rtpn_batch_create(ctypes.byref(p), n, ctypes.cast(Ns, _P), ctypes.cast(nx, _P),
+                                     ctypes.cast(ny, _P), ctypes.cast(nz, _P), ctypes.cast(hs, _P),
+                                     ctypes.cast(bcs, _P), ctypes.cast(dts, _P), PRECISION[precision])
+        if rc != OK:
+            raise RtpnError(rc, lib().rtpn_last_error(None).decode() or lib().rtpn_strerror(rc).decode())
+        self._p = p
+        self.instances = [_Instance(lib().rtpn_batch_instance(p, i), inst[i][0], inst[i][1],
+                                    inst[i][2], inst[i][3], precision) for i in range(n)]
+
+    def _chk(self, rc):
+        if rc != OK:
+            raise RtpnError(rc, lib().rtpn_batch_last_error(self._p).decode() or
+                            lib().rtpn_strerror(rc).decode())
+
+    def __len__(self):
+        return len(self.instances)
+
+    def __getitem__(self, i) -> Context:
+        return self.instances[i]
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        self._chk(lib().rtpn_batch_set_stream(self._p, _P(handle or 0)))
+
+    def set_tile(self, tile):
+        self._chk(lib().rtpn_batch_set_tile(self._p, *tile))
+
+    def tile(self):
+        t = [_I(), _I(), _I()]
+        self._chk(lib().rtpn_batch_get_tile(self._p, *[ctypes.byref(v) for v in t]))
+        return tuple(v.value for v in t)
+
+    def step(self, k: int = 1):
+        self._chk(lib().rtpn_batch_step(self._p, int(k)))
+
+    def autotune(self, reps: int = 2):
+        tile = (_I * 3)()
+        ms = _D()
+        self._chk(lib().rtpn_batch_autotune(self._p, int(reps), tile, ctypes.byref(ms)))
+        return tuple(tile), ms.value
+
+    def step_looped(self, k: int = 1):
+        self._chk(lib().rtpn_batch_step_looped(self._p, int(k)))
+
+    def synchronize(self):
+        self._chk(lib().rtpn_batch_synchronize(self._p))
+
+    def close(self):
+        if getattr(self, "_p", None):
+            for i in self.instances:
+                i._p = None
+            lib().rtpn_batch_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,86 @@
+"""Adjoint form: GPU discrete adjoint vs the oracle's discrete adjoint and vs central finite
+differences of the GPU forward.
+
+Bounds: FP64 storage <= 1e-12 relative to the oracle (max norm over each gradient); FP32 storage
+<= 1e-4 relative to the oracle's exact adjoint; FP32 adjoint vs FP64 central differences <= 1e-3.
+"""
+import numpy as np
+import pytest
+
+from oracle import stepper as st
+from paper_2004_02833_gb300 import rtpn, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("bc", ["periodic", "vacuum"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_adjoint_matches_oracle(cuda_device, coupling_cache, bc, precision, tol):
+    N, shape = 3, (5, 6, 8)
+    inst, u0 = synth.random_instance(N, shape, seed=41, bc=bc)
+    w = np.random.default_rng(42).uniform(0.0, 1.0, shape)
+    mats, slots = coupling_cache(N)
+    P = st.Problem(N, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, bc, mats=mats, slots=slots)
+    J_ref, gsa_ref, gss_ref, gq_ref = P.gradient(u0, 5, w)
+    with rtpn.Context(N, shape, inst.h, bc, precision, inst.dt) as ctx:
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        J, (gsa, gss, gq) = ctx.adjoint(w, 5, ckpt_every=2)
+        final = ctx.get_moments()
+    assert abs(J - J_ref) <= tol * abs(J_ref)
+    assert rel(gsa, gsa_ref) <= tol and rel(gss, gss_ref) <= tol and rel(gq, gq_ref) <= tol
+    assert rel(final, P.run(u0, 5)) <= max(tol, 1e-12)
+
+
+def test_adjoint_p3_32_checkerboard_fp64(cuda_device, coupling_cache):
+    # P3 on 32^3 in FP64: the lattice scaled to 32^3, vacuum, zero start, detector box scaled
+    inst = synth.checkerboard(3, 32)
+    w = synth.detector_box(32)
+    mats, slots = coupling_cache(3)
+    P = st.Problem(3, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, inst.bc, mats=mats, slots=slots)
+    k = 30
+    J_ref, gsa_ref, gss_ref, gq_ref = P.gradient(inst.full_state(), k, w)
+    with rtpn.Context(3, inst.shape, inst.h, inst.bc, "fp64", inst.dt) as ctx:
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        J, (gsa, gss, gq) = ctx.adjoint(w, k, ckpt_every=7)
+    assert J_ref > 0 and abs(J - J_ref) <= 1e-12 * J_ref
+    assert rel(gsa, gsa_ref) <= 1e-12 and rel(gss, gss_ref) <= 1e-12 and rel(gq, gq_ref) <= 1e-12
+
+
+def test_adjoint_fp32_vs_central_differences(cuda_device):
+    # P15 on the [0,7]^3 lattice at 48^3 (long enough for the source to reach the detector):
+    # the FP32 adjoint against central differences of the FP64 GPU forward at seeded cells.
+    N, n, k = 15, 48, 100
+    inst = synth.checkerboard(N, n)
+    w = synth.detector_box(n)
+    with rtpn.Context(N, inst.shape, inst.h, inst.bc, "fp32", inst.dt) as ctx:
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        J32, (gsa, gss, gq) = ctx.adjoint(w, k, ckpt_every=20)
+
+    def J64(sa, ss, q):
+        with rtpn.Context(N, inst.shape, inst.h, inst.bc, "fp64", inst.dt) as c:
+            c.set_media(sa, ss, q)
+            c.step(k)
+            return float(np.sum(w * c.get_component(0)))
+
+    base = J64(inst.sigma_a, inst.sigma_s, inst.q)
+    assert base > 0 and abs(J32 - base) <= 1e-4 * base
+    rng = np.random.default_rng(4)
+    # cells between the source block (3,3,3) and the detector block (5,3,3)
+    cells = [(int(z), int(y), int(x)) for z, y, x in
+             zip(rng.integers(22, 26, 3), rng.integers(22, 26, 3), rng.integers(26, 34, 3))]
+    for cell in cells:
+        for name, g in (("sa", gsa), ("ss", gss), ("q", gq)):
+            args = {"sa": inst.sigma_a, "ss": inst.sigma_s, "q": inst.q}
+            eps = 1e-6 * max(float(args[name][cell]), 1.0)
+            p = {kk: v.copy() for kk, v in args.items()}
+            m = {kk: v.copy() for kk, v in args.items()}
+            p[name][cell] += eps
+            m[name][cell] -= eps
+            fd = (J64(p["sa"], p["ss"], p["q"]) - J64(m["sa"], m["ss"], m["q"])) / (2 * eps)
+            scale = max(abs(fd), 1e-3 * np.abs(g).max())
+            assert abs(g[cell] - fd) <= 1e-3 * scale, (name, cell, g[cell], fd)

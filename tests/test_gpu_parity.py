@@ -36,7 +36,7 @@ def oracle_problem(inst, coupling_cache):
 
 def gpu_run(inst, u0, k, precision, kernel="auto", tile=(0, 0, 0), chunks=None):
     with rtpn.Context(inst.N, inst.shape, inst.h, inst.bc, precision, inst.dt) as ctx:
-        if kernel != "auto":
+        if kernel != "auto" or any(tile):
             ctx.set_kernel(kernel, tile)
         ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
         ctx.set_moments(u0)
@@ -198,3 +198,67 @@ def test_unsupported_kernel_rejected(cuda_device):
             ctx.set_kernel("window")
         with pytest.raises(rtpn.RtpnError):
             ctx.set_kernel("window", (33, 1, 1))
+
+
+def test_autotune_keeps_state_and_picks_a_valid_tile(cuda_device, coupling_cache):
+    inst, u0 = synth.random_instance(7, (8, 10, 64), seed=21, bc="periodic")
+    ref = oracle_problem(inst, coupling_cache).run(u0, 2)
+    with rtpn.Context(7, inst.shape, inst.h, inst.bc, "fp32", inst.dt) as ctx:
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        tile, ms = ctx.autotune(reps=1)
+        assert tile[0] * tile[1] * tile[2] % 32 == 0 and ms > 0
+        assert np.array_equal(ctx.get_moments(), u0.astype(np.float32).astype(np.float64))
+        ctx.step(2)
+        got = ctx.get_moments()
+    assert rel_err(got, ref) <= TOL["fp32"]
+
+
+STAGE_CASES = [
+    # N, shape (nz, ny, nx) with nx a multiple of 8, bc, tile (0 = default)
+    (7, (9, 13, 72), "vacuum", (0, 0, 0)),
+    (7, (5, 6, 32), "periodic", (0, 0, 0)),
+    (15, (7, 9, 40), "periodic", (0, 0, 0)),
+    (15, (3, 5, 8), "vacuum", (0, 0, 0)),
+    (39, (5, 6, 8), "periodic", (32, 2, 2)),
+    (39, (5, 7, 8), "vacuum", (40, 2, 2)),
+    (39, (3, 5, 80), "periodic", (40, 2, 2)),
+    (39, (4, 3, 72), "vacuum", (32, 2, 2)),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("N,shape,bc,tile", STAGE_CASES)
+def test_stage_kernel(cuda_device, coupling_cache, N, shape, bc, tile, precision):
+    # TMA-staged kernel: full and partial tiles, wrapped and zero-filled halos
+    inst, u0 = synth.random_instance(N, shape, seed=300 + N, bc=bc)
+    ref = oracle_problem(inst, coupling_cache).run(u0, 3)
+    got = gpu_run(inst, u0, 3, precision, kernel="stage", tile=tile)
+    assert rel_err(got, ref) <= TOL[precision], rel_err(got, ref)
+
+
+def test_stage_kernel_long_run_matches_window(cuda_device):
+    inst, u0 = synth.random_instance(39, (6, 8, 40), seed=5, bc="periodic")
+    a = gpu_run(inst, u0, 20, "fp32", kernel="stage")
+    b = gpu_run(inst, u0, 20, "fp32", kernel="window")
+    assert rel_err(a, b) <= 1e-6
+
+
+def test_stage_wait_timeout_is_reported(cuda_device, coupling_cache):
+    # a bounded mbarrier wait that runs out (its copies are never issued) sets the status word,
+    # the CTAs leave, the host reads RTPN_ETIMEOUT and the context stays usable
+    inst, u0 = synth.random_instance(7, (4, 6, 32), seed=8, bc="periodic")
+    ref = oracle_problem(inst, coupling_cache).run(u0, 2)
+    with rtpn.Context(7, inst.shape, inst.h, inst.bc, "fp32", inst.dt) as ctx:
+        ctx.set_kernel("stage")
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        assert rtpn.lib().rtpn_test_wait_timeout(ctx._p, 0, 2000) == rtpn.OK
+        with pytest.raises(rtpn.RtpnError) as e:
+            ctx.synchronize()
+        assert e.value.code == rtpn.ETIMEOUT
+        ctx.synchronize()  # the flag was cleared
+        ctx.set_moments(u0)
+        ctx.step(2)
+        got = ctx.get_moments()
+    assert rel_err(got, ref) <= TOL["fp32"]
