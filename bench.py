@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     p.add_argument("--kernel", default="auto", choices=["auto", "generic", "window", "stage"])
     p.add_argument("--tile", default="0,0,0")
+    p.add_argument("--chunks", type=int, default=0, help="threads per cell of the staged kernel")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true",
@@ -179,8 +180,8 @@ def main():
     stream = torch.cuda.Stream()
     ctx = rtpn.Context(args.N, inst.shape, inst.h, inst.bc, args.precision, inst.dt)
     ctx.set_stream(stream)
-    if args.kernel != "auto" or any(tile):
-        ctx.set_kernel(args.kernel, tile)
+    if args.kernel != "auto" or any(tile) or args.chunks:
+        ctx.set_kernel(args.kernel, tile, args.chunks)
     info = ctx.info()
     with torch.cuda.stream(stream):
         media = [torch.tensor(a, dtype=torch.float32, device="cuda")
@@ -251,7 +252,8 @@ def main():
             "data": "synthetic", "config": workload_config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": 2 * args.steps + 1, "nonfinite": nonfinite, "forms": forms,
-            "kernel_used": {1: "generic", 2: "window", 3: "stage"}.get(ctx.info().kernel, "?")}
+            "kernel_used": {1: "generic", 2: "window", 3: "stage"}.get(ctx.info().kernel, "?"),
+            "tile": list(ctx.info().tile), "chunks": ctx.info().chunks}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -315,7 +317,7 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
             b.set_stream(stream)
             for c, i in zip(b.instances, insts):
                 c.set_media(i.sigma_a, i.sigma_s, i.q)
-                c.set_moments(i.full_state())
+                c.set_component(0, i.u0)  # every other moment starts at 0 (fresh context)
             if mode == "grouped":
                 tile, _ = b.autotune(reps=1)
                 res["tile"] = tile

@@ -41,11 +41,11 @@ def window_orders() -> list[int]:
     return [int(v) for v in re.findall(r"X\((\d+)\)", line)]
 
 
-def stage_variants() -> list[tuple[int, int, int, int]]:
+def stage_variants() -> list[tuple[int, int, int, int, int]]:
     text = open(os.path.join(CSRC, "stage_variants.h")).read()
     line = [l for l in text.splitlines() if l.startswith("#define RTPN_STAGE_VARIANTS")][0]
     return [tuple(int(v) for v in m) for m in
-            re.findall(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", line)]
+            re.findall(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", line)]
 
 
 def units() -> list[tuple[str, list[str], str]]:
@@ -59,17 +59,18 @@ def units() -> list[tuple[str, list[str], str]]:
         for cls in (0, 1):
             out.append((os.path.join(CSRC, VARIANT_SRC), [f"-DRTPN_WN={n}", f"-DRTPN_WCLS={cls}"],
                         f"window_N{n}_c{cls}.o"))
-    for n, tx, ty, tz in stage_variants():
+    for n, tx, ty, tz, sp in stage_variants():
         out.append((os.path.join(CSRC, STAGE_SRC),
-                    [f"-DRTPN_SN={n}", f"-DRTPN_STX={tx}", f"-DRTPN_STY={ty}", f"-DRTPN_STZ={tz}"],
-                    f"stage_N{n}_{tx}x{ty}x{tz}.o"))
+                    [f"-DRTPN_SN={n}", f"-DRTPN_STX={tx}", f"-DRTPN_STY={ty}", f"-DRTPN_STZ={tz}",
+                     f"-DRTPN_SSPLIT={sp}"],
+                    f"stage_N{n}_{tx}x{ty}x{tz}_s{sp}.o"))
     return out
 
 
 def _compile(unit, extra: list[str]) -> str:
     src, defines, name = unit
     obj = os.path.join(BUILD_DIR, name)
-    deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "rtpn.h"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj

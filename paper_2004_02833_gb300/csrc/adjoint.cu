@@ -248,7 +248,7 @@ __global__ void k_copy_cast(const A* __restrict__ in, B* __restrict__ out, long 
         out[i] = (B)in[i];
 }
 
-unsigned blocks_for(long long V) { return (unsigned)((V + 255) / 256); }
+unsigned blocks_for(long long V, int threads = 256) { return (unsigned)((V + threads - 1) / threads); }
 
 }  // namespace
 
@@ -400,11 +400,11 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
             const int cls = (p % 3 == 1) ? 0 : 1;
             const int ofs = (p % 3 == 1) ? FAC_FULL : FAC_HALF;
             const S* pre = (const S*)((char*)seg.p + (size_t)p * state);
-            k_adj_targets<S, F><<<blocks_for(V), 128, 0, st>>>(pre, (F*)lam.p, (F*)wbuf.p, (const F*)ctx->fac,
+            k_adj_targets<S, F><<<blocks_for(V, 128), 128, 0, st>>>(pre, (F*)lam.p, (F*)wbuf.p, (const F*)ctx->fac,
                                                                (const F*)dfac.p, tf[cls], g, ofs,
                                                                ctx->media + 2 * V, (double*)gacc.p,
                                                                (double*)gqb.p);
-            k_adj_sources<F><<<blocks_for(V), 128, 0, st>>>((F*)lam.p, (const F*)wbuf.p, tt[1 - cls].tab,
+            k_adj_sources<F><<<blocks_for(V, 128), 128, 0, st>>>((F*)lam.p, (const F*)wbuf.p, tt[1 - cls].tab,
                                                             tf[cls].a0, g);
         }
     }

@@ -295,7 +295,7 @@ int choose_kernel(rtpn_ctx* ctx) {
     if (k == RTPN_KERNEL_AUTO) {
         const bool tile_set = ctx->tx || ctx->ty || ctx->tz;
         if (kStageInAuto && stage_supported(ctx->N, ctx->prec, ctx->g.nx) &&
-            (!tile_set || stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz)))
+            (!tile_set || stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->chunks)))
             k = RTPN_KERNEL_STAGE;
         else
             k = window_supported(ctx->N, ctx->prec) ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
@@ -304,9 +304,9 @@ int choose_kernel(rtpn_ctx* ctx) {
         if (!stage_supported(ctx->N, ctx->prec, ctx->g.nx))
             return fail(ctx, RTPN_EUNSUPPORTED,
                         "staged kernel not compiled for this N/precision or nx*elem not 16-byte rows");
-        if ((ctx->tx || ctx->ty || ctx->tz) && !stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz))
-            return fail(ctx, RTPN_EUNSUPPORTED, "no staged kernel compiled for this tile");
-        int rc = stage_prepare(ctx, ctx->tx, ctx->ty, ctx->tz);
+        if (!stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->chunks))
+            return fail(ctx, RTPN_EUNSUPPORTED, "no staged kernel compiled for this tile / chunk count");
+        int rc = stage_prepare(ctx, ctx->tx, ctx->ty, ctx->tz, ctx->chunks);
         if (rc) return fail(ctx, RTPN_ECUDA, std::string("staged kernel set-up: ") +
                                                  cudaGetErrorString((cudaError_t)rc));
     }
@@ -423,9 +423,9 @@ int rtpn_create(rtpn_ctx** out, int N, int nx, int ny, int nz, double h, int bc,
     if (e != cudaSuccess) return bail(fail(ctx, RTPN_ENOMEM, "scratch allocation failed"));
     e = cudaMalloc(&ctx->counter, sizeof(unsigned long long));
     if (e != cudaSuccess) return bail(fail(ctx, RTPN_ENOMEM, "scratch allocation failed"));
-    e = cudaMalloc(&ctx->status, sizeof(unsigned));
+    e = cudaMalloc(&ctx->status, 8 * sizeof(unsigned));
     if (e != cudaSuccess) return bail(fail(ctx, RTPN_ENOMEM, "status allocation failed"));
-    e = cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream);
+    e = cudaMemsetAsync(ctx->status, 0, 8 * sizeof(unsigned), ctx->stream);
     if (e != cudaSuccess) return bail(fail(ctx, RTPN_ECUDA, cudaGetErrorString(e)));
     if ((rc = upload_tables(ctx))) return bail(rc);
     e = cudaMemsetAsync(ctx->u, 0, (size_t)ctx->md.nc * V * ctx->elem, ctx->stream);
@@ -452,7 +452,12 @@ int rtpn_set_stream(rtpn_ctx* ctx, void* stream) {
 }
 
 int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z) {
+    return rtpn_set_kernel_ex(ctx, kernel, tile_x, tile_y, tile_z, 0);
+}
+
+int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z, int chunks) {
     if (!ctx) return RTPN_EINVAL;
+    if (chunks < 0 || chunks > 64) return fail(ctx, RTPN_EINVAL, "bad chunk count");
     if (kernel < RTPN_KERNEL_AUTO || kernel > RTPN_KERNEL_STAGE)
         return fail(ctx, RTPN_EINVAL, "unknown kernel");
     if (tile_x < 0 || tile_y < 0 || tile_z < 0) return fail(ctx, RTPN_EINVAL, "bad tile");
@@ -462,12 +467,13 @@ int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_
         if (th > 256 || th % 32 != 0)
             return fail(ctx, RTPN_EINVAL, "tile must hold a multiple of 32 threads, at most 256");
     }
-    const int old = ctx->kernel, ox = ctx->tx, oy = ctx->ty, oz = ctx->tz;
+    const int old = ctx->kernel, ox = ctx->tx, oy = ctx->ty, oz = ctx->tz, oc = ctx->chunks;
     ctx->kernel = kernel;
     drop_graphs(ctx);
     ctx->tx = tile_x;
     ctx->ty = tile_y;
     ctx->tz = tile_z;
+    ctx->chunks = kernel == RTPN_KERNEL_STAGE || kernel == RTPN_KERNEL_AUTO ? chunks : 0;
     int rc = choose_kernel(ctx);
     if (rc) {
         const std::string msg = ctx->err;
@@ -475,6 +481,7 @@ int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_
         ctx->tx = ox;
         ctx->ty = oy;
         ctx->tz = oz;
+        ctx->chunks = oc;
         choose_kernel(ctx);
         ctx->err = msg;
     }
@@ -632,13 +639,17 @@ int rtpn_count_nonfinite(rtpn_ctx* ctx, long long* out) {
 int rtpn_synchronize(rtpn_ctx* ctx) {
     if (!ctx) return RTPN_EINVAL;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    unsigned st = 0;
-    CUDA_TRY(ctx, cudaMemcpy(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost));
-    if (st) {
-        CUDA_TRY(ctx, cudaMemset(ctx->status, 0, sizeof(unsigned)));
-        if (st & 1u) return fail(ctx, RTPN_ETIMEOUT, "a bounded wait in a staged kernel ran out");
-        return fail(ctx, RTPN_ECUDA, "a staged-kernel self-check failed (status " + std::to_string(st) + ")");
+    unsigned st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    CUDA_TRY(ctx, cudaMemcpy(st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st[0]) {
+        std::string rec;
+        for (int i = 0; i < 8; ++i) rec += (i ? " " : "") + std::to_string(st[i]);
+        CUDA_TRY(ctx, cudaMemset(ctx->status, 0, sizeof(st)));
+        if (st[0] & 1u)
+            return fail(ctx, RTPN_ETIMEOUT, "a bounded wait in a staged kernel ran out [" + rec + "]");
+        return fail(ctx, RTPN_ECUDA, "a staged-kernel self-check failed [" + rec + "]");
     }
+    CUDA_TRY(ctx, cudaMemset(ctx->status, 0, sizeof(st)));
     return RTPN_OK;
 }
 
@@ -670,6 +681,10 @@ int rtpn_get_info(const rtpn_ctx* ctx, rtpn_info* out) {
     out->state_bytes = (size_t)ctx->md.nc * ctx->g.V * ctx->elem;
     out->factor_bytes = (size_t)FAC_PLANES * ctx->g.V * (ctx->prec == RTPN_FP64 ? 8 : 4);
     out->steps_done = ctx->steps_done;
+    out->tile[0] = ctx->tx;
+    out->tile[1] = ctx->ty;
+    out->tile[2] = ctx->tz;
+    out->chunks = ctx->active_kernel == RTPN_KERNEL_STAGE ? ctx->chunks : 1;
     return RTPN_OK;
 }
 

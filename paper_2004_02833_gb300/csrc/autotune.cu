@@ -20,6 +20,7 @@ namespace {
 
 struct Tile {
     int x, y, z;
+    int c = 0;  // threads per cell (staged kernel), 0 = not applicable
 };
 
 const Tile kCandidates[] = {{32, 1, 1},  {32, 2, 1}, {32, 4, 1}, {32, 8, 1}, {32, 1, 2}, {32, 2, 2},
@@ -44,7 +45,7 @@ void load_file() {
         std::istringstream in(line.substr(bar + 1));
         Tile t;
         double ms;
-        if (in >> t.x >> t.y >> t.z >> ms) g_cache[line.substr(0, bar)] = {t, ms};
+        if (in >> t.x >> t.y >> t.z >> t.c >> ms) g_cache[line.substr(0, bar)] = {t, ms};
     }
 }
 
@@ -52,7 +53,7 @@ void store_file(const std::string& key, Tile t, double ms) {
     const char* path = std::getenv("RTPN_TUNE_CACHE");
     if (!path) return;
     std::ofstream f(path, std::ios::app);
-    f << key << "|" << t.x << " " << t.y << " " << t.z << " " << ms << "\n";
+    f << key << "|" << t.x << " " << t.y << " " << t.z << " " << t.c << " " << ms << "\n";
 }
 
 std::string device_key() {
@@ -65,12 +66,13 @@ std::string device_key() {
 
 // Times `reps` pass pairs for every candidate via `run_pair(stream)`; `set_tile(t)` applies one.
 template <typename SetTile, typename RunPair>
-int sweep(cudaStream_t st, int reps, SetTile set_tile, RunPair run_pair, Tile* best, double* best_ms) {
+int sweep(cudaStream_t st, int reps, const std::vector<Tile>& cands, SetTile set_tile, RunPair run_pair,
+          Tile* best, double* best_ms) {
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return RTPN_ECUDA;
     *best_ms = -1.0;
     int rc = RTPN_OK;
-    for (const Tile& t : kCandidates) {
+    for (const Tile& t : cands) {
         if (set_tile(t) != RTPN_OK) continue;  // tile not valid for this object
         if ((rc = run_pair(st))) break;        // warm-up
         cudaEventRecord(a, st);
@@ -105,15 +107,16 @@ int rtpn_autotune(rtpn_ctx* ctx, int reps, int tile[3], double* ms_per_step) {
         ctx->err = "rtpn_set_media has not been called";
         return RTPN_ESTATE;
     }
-    if (ctx->active_kernel != RTPN_KERNEL_WINDOW) {
-        ctx->err = "the autotuner tunes the window kernel, which is not active";
+    if (ctx->active_kernel != RTPN_KERNEL_WINDOW && ctx->active_kernel != RTPN_KERNEL_STAGE) {
+        ctx->err = "the autotuner tunes the window and staged kernels, neither is active";
         return RTPN_EUNSUPPORTED;
     }
+    const int kernel = ctx->active_kernel;
     std::ostringstream k;
-    k << "single N=" << ctx->N << " prec=" << ctx->prec << " bc=" << ctx->g.bc << " grid="
+    k << "single kernel=" << kernel << " N=" << ctx->N << " prec=" << ctx->prec << " bc=" << ctx->g.bc << " grid="
       << ctx->g.nx << "x" << ctx->g.ny << "x" << ctx->g.nz << " dev=" << device_key();
     const std::string key = k.str();
-    Tile best{ctx->tx, ctx->ty, ctx->tz};
+    Tile best{ctx->tx, ctx->ty, ctx->tz, ctx->chunks};
     double best_ms = -1.0;
     {
         std::lock_guard<std::mutex> lock(g_mu);
@@ -124,6 +127,14 @@ int rtpn_autotune(rtpn_ctx* ctx, int reps, int tile[3], double* ms_per_step) {
             best_ms = it->second.second;
         }
     }
+    std::vector<Tile> cands;
+    if (kernel == RTPN_KERNEL_STAGE) {
+        int v[4 * 64];
+        const int n = rtpn::stage_variants_of(ctx->N, v, 64);
+        for (int i = 0; i < n; ++i) cands.push_back({v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]});
+    } else {
+        for (const Tile& t : kCandidates) cands.push_back(t);
+    }
     if (best_ms < 0) {
         const size_t bytes = (size_t)ctx->md.nc * ctx->g.V * ctx->elem;
         void* snap = nullptr;
@@ -133,10 +144,10 @@ int rtpn_autotune(rtpn_ctx* ctx, int reps, int tile[3], double* ms_per_step) {
             return RTPN_ENOMEM;
         }
         cudaMemcpyAsync(snap, ctx->u, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
-        const int otx = ctx->tx, oty = ctx->ty, otz = ctx->tz;
+        const int otx = ctx->tx, oty = ctx->ty, otz = ctx->tz, oc = ctx->chunks;
         int rc = sweep(
-            ctx->stream, reps,
-            [&](Tile t) { return rtpn_set_kernel(ctx, RTPN_KERNEL_WINDOW, t.x, t.y, t.z); },
+            ctx->stream, reps, cands,
+            [&](Tile t) { return rtpn_set_kernel_ex(ctx, kernel, t.x, t.y, t.z, t.c); },
             [&](cudaStream_t) {
                 int r = rtpn_substep(ctx, 0, 0);
                 return r ? r : rtpn_substep(ctx, 1, 0);
@@ -146,14 +157,14 @@ int rtpn_autotune(rtpn_ctx* ctx, int reps, int tile[3], double* ms_per_step) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(snap);
         if (rc) {
-            rtpn_set_kernel(ctx, RTPN_KERNEL_WINDOW, otx, oty, otz);
+            rtpn_set_kernel_ex(ctx, kernel, otx, oty, otz, oc);
             return rc;
         }
         std::lock_guard<std::mutex> lock(g_mu);
         g_cache[key] = {best, best_ms};
         store_file(key, best, best_ms);
     }
-    int rc = rtpn_set_kernel(ctx, RTPN_KERNEL_WINDOW, best.x, best.y, best.z);
+    int rc = rtpn_set_kernel_ex(ctx, kernel, best.x, best.y, best.z, best.c);
     if (rc) return rc;
     if (tile) {
         tile[0] = best.x;
@@ -208,8 +219,9 @@ int rtpn_batch_autotune(rtpn_batch* b, int reps, int tile[3], double* ms_per_ste
             off += nb;
         }
         Tile old = best;
+        const std::vector<Tile> cands(std::begin(kCandidates), std::end(kCandidates));
         int rc = sweep(
-            st, reps, [&](Tile t) { return rtpn_batch_set_tile(b, t.x, t.y, t.z); },
+            st, reps, cands, [&](Tile t) { return rtpn_batch_set_tile(b, t.x, t.y, t.z); },
             [&](cudaStream_t) { return rtpn_batch_step(b, 1); }, &best, &best_ms);
         off = 0;
         for (size_t i = 0; i < ctxs.size(); ++i) {

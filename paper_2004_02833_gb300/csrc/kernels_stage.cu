@@ -10,25 +10,28 @@
 namespace rtpn {
 namespace stg {
 
-#define RTPN_SDECL(n, x, y, z)                                                                       \
-    int stage_launch_##n##_##x##_##y##_##z(int, int, const Args&, int, cudaStream_t);               \
-    int stage_smem_##n##_##x##_##y##_##z(int, int);
+#define RTPN_SDECL(n, x, y, z, p)                                                                  \
+    int stage_launch_##n##_##x##_##y##_##z##_##p(int, int, const Args&, int, cudaStream_t);          \
+    int stage_smem_##n##_##x##_##y##_##z##_##p(int, int);
 RTPN_STAGE_VARIANTS(RTPN_SDECL)
 #undef RTPN_SDECL
 
 struct Variant {
-    int N, tx, ty, tz;
+    int N, tx, ty, tz, split;
     int (*launch)(int, int, const Args&, int, cudaStream_t);
     int (*smem)(int, int);
 };
-#define RTPN_SENTRY(n, x, y, z) \
-    Variant{n, x, y, z, stage_launch_##n##_##x##_##y##_##z, stage_smem_##n##_##x##_##y##_##z},
+#define RTPN_SENTRY(n, x, y, z, p)                                                      \
+    Variant{n, x, y, z, p, stage_launch_##n##_##x##_##y##_##z##_##p, stage_smem_##n##_##x##_##y##_##z##_##p},
 static const Variant kVariants[] = {RTPN_STAGE_VARIANTS(RTPN_SENTRY)};
 #undef RTPN_SENTRY
 
-static const Variant* find(int N, int tx, int ty, int tz) {
+// first compiled variant of order N with this tile (0 = any) and split (0 = any)
+static const Variant* find(int N, int tx, int ty, int tz, int split = 0) {
     for (const auto& v : kVariants)
-        if (v.N == N && (tx == 0 || (v.tx == tx && v.ty == ty && v.tz == tz))) return &v;
+        if (v.N == N && (tx == 0 || (v.tx == tx && v.ty == ty && v.tz == tz)) &&
+            (split == 0 || v.split == split))
+            return &v;
     return nullptr;
 }
 
@@ -47,13 +50,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 static bool make_map(CUtensorMap* m, void* base, int precision, const rtpn::Geom& g, int nc, int bx, int by,
-                     int bz) {
+                     int bz, int bc) {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t es = precision == RTPN_BF16 ? 2 : 4;
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)nc};
     const cuuint64_t strides[3] = {g.nx * es, (cuuint64_t)g.nx * g.ny * es, (cuuint64_t)g.V * es};
-    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, (cuuint32_t)bc};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = fn(m, precision == RTPN_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                     4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -69,24 +72,31 @@ bool stage_supported(int N, int precision, int nx) {
     return nx % hx == 0;
 }
 
-bool stage_has_tile(int N, int tx, int ty, int tz) { return stg::find(N, tx, ty, tz) != nullptr; }
+bool stage_has_tile(int N, int tx, int ty, int tz, int split) {
+    return stg::find(N, tx, ty, tz, split) != nullptr;
+}
 
-int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz) {
-    const stg::Variant* v = stg::find(ctx->N, tx, ty, tz);
+int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int split) {
+    const stg::Variant* v = stg::find(ctx->N, tx, ty, tz, split);
     if (!v) return (int)cudaErrorNotSupported;
-    // the wider default tile when it divides nx exactly
+    // default (no tile given): the first listed variant whose width divides nx, else the first one
     if (tx == 0)
         for (const auto& w : stg::kVariants)
-            if (w.N == ctx->N && ctx->g.nx % w.tx == 0 && w.tx > v->tx) v = &w;
+            if (w.N == ctx->N && (split == 0 || w.split == split) && ctx->g.nx % w.tx == 0) {
+                v = &w;
+                break;
+            }
     const int es = ctx->prec == RTPN_BF16 ? 2 : 4;
     const int hx = 16 / es;
     // the four tensor maps live in device global memory (64-byte aligned) and the kernel reads
-    // them from there: tile box, x-halo group, y-halo row, z-halo plane
+    // them from there: tile box, x-halo group, y-halo row, z-halo plane, each spanning the N/2 + 1
+    // consecutive components of a (type, |m|) run
+    const int nl = ctx->N / 2 + 1;
     alignas(64) CUtensorMap maps[4];
-    if (!stg::make_map(&maps[0], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, v->tz) ||
-        !stg::make_map(&maps[1], ctx->u, ctx->prec, ctx->g, ctx->md.nc, hx, v->ty, v->tz) ||
-        !stg::make_map(&maps[2], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, 1, v->tz) ||
-        !stg::make_map(&maps[3], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, 1))
+    if (!stg::make_map(&maps[0], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, v->tz, nl) ||
+        !stg::make_map(&maps[1], ctx->u, ctx->prec, ctx->g, ctx->md.nc, hx, v->ty, v->tz, nl) ||
+        !stg::make_map(&maps[2], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, 1, v->tz, nl) ||
+        !stg::make_map(&maps[3], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, 1, nl))
         return (int)cudaErrorInvalidValue;
     if (!ctx->stage_maps_dev) {
         cudaError_t e = cudaMalloc(&ctx->stage_maps_dev, sizeof(maps));
@@ -134,7 +144,22 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz) {
     ctx->tx = v->tx;
     ctx->ty = v->ty;
     ctx->tz = v->tz;
+    ctx->chunks = v->split;
     return 0;
+}
+
+// the compiled (tile, split) choices of order N, for the tuner
+int stage_variants_of(int N, int* tiles, int max) {
+    int n = 0;
+    for (const auto& v : stg::kVariants)
+        if (v.N == N && n < max) {
+            tiles[4 * n] = v.tx;
+            tiles[4 * n + 1] = v.ty;
+            tiles[4 * n + 2] = v.tz;
+            tiles[4 * n + 3] = v.split;
+            ++n;
+        }
+    return n;
 }
 
 int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long skip_stage,

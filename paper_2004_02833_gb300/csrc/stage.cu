@@ -2,23 +2,28 @@
 // RTPN_STZ, both target classes, FP32 and BF16 storage.  kernels_stage.cu dispatches to it.
 #include "stage_impl.cuh"
 
-#if !defined(RTPN_SN) || !defined(RTPN_STX) || !defined(RTPN_STY) || !defined(RTPN_STZ)
-#error "compile with -DRTPN_SN=<order> -DRTPN_STX=.. -DRTPN_STY=.. -DRTPN_STZ=.."
+#if !defined(RTPN_SN) || !defined(RTPN_STX) || !defined(RTPN_STY) || !defined(RTPN_STZ) || !defined(RTPN_SSPLIT)
+#error "compile with -DRTPN_SN=<order> -DRTPN_STX=.. -DRTPN_STY=.. -DRTPN_STZ=.. -DRTPN_SSPLIT=.."
 #endif
 
-#define RTPN_SCAT2(a, b, c, d, e) a##_##b##_##c##_##d##_##e
-#define RTPN_SCAT(a, b, c, d, e) RTPN_SCAT2(a, b, c, d, e)
-#define RTPN_SVARIANT(name) RTPN_SCAT(name, RTPN_SN, RTPN_STX, RTPN_STY, RTPN_STZ)
+#define RTPN_SCAT2(a, b, c, d, e, f) a##_##b##_##c##_##d##_##e##_##f
+#define RTPN_SCAT(a, b, c, d, e, f) RTPN_SCAT2(a, b, c, d, e, f)
+#define RTPN_SVARIANT(name) RTPN_SCAT(name, RTPN_SN, RTPN_STX, RTPN_STY, RTPN_STZ, RTPN_SSPLIT)
 
 namespace rtpn {
 namespace stg {
 
-constexpr int kN = RTPN_SN, kTX = RTPN_STX, kTY = RTPN_STY, kTZ = RTPN_STZ;
+// Everything but the uniquely named entry points has internal linkage: every variant of this file
+// defines a k_stage / launch_one of the same name, and the linker must not merge them.
+namespace {
+
+constexpr int kN = RTPN_SN, kTX = RTPN_STX, kTY = RTPN_STY, kTZ = RTPN_STZ, kSplit = RTPN_SSPLIT;
+constexpr int kThreads = kTX * kTY * kTZ * kSplit;
 
 template <int A, typename S>
-__global__ void __launch_bounds__(kTX * kTY * kTZ, 1) k_stage(Args a) {
+__global__ void __launch_bounds__(kThreads, 1) k_stage(Args a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    stage_kernel_body<kN, A, S, kTX, kTY, kTZ>(a, smem);
+    stage_kernel_body<kN, A, S, kTX, kTY, kTZ, kSplit>(a, smem);
 }
 
 template <int A, typename S>
@@ -35,16 +40,17 @@ int launch_one(const Args& a, int sms, cudaStream_t st) {
         configured[dev] = true;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<A, S>,
-                                                                  kTX * kTY * kTZ, L::BYTES);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<A, S>, kThreads, L::BYTES);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) return (int)cudaErrorLaunchOutOfResources;
     long long grid = (long long)per_sm * sms;
     if (grid > a.tiles) grid = a.tiles;
     if (grid < 1) return 0;
-    k_stage<A, S><<<(unsigned)grid, kTX * kTY * kTZ, L::BYTES, st>>>(a);
+    k_stage<A, S><<<(unsigned)grid, kThreads, L::BYTES, st>>>(a);
     return (int)cudaGetLastError();
 }
+
+}  // namespace
 
 int RTPN_SVARIANT(stage_launch)(int cls, int precision, const Args& a, int sms, cudaStream_t st) {
     if (precision == RTPN_BF16)

@@ -63,25 +63,31 @@ __host__ __device__ constexpr int pad128(int bytes) { return (bytes + 127) / 128
 template <int N, int A, typename S, int TX, int TY, int TZ>
 struct Layout {
     static constexpr int B = 1 - A;
-    static constexpr int NL = N / 2 + 1;
-    static constexpr int SLOTS = 2 * NL;  // (type, l/2) slots of a column
+    static constexpr int NL = N / 2 + 1;  // components per (type, |m|) run, at most
     static constexpr int ES = (int)sizeof(S);
     static constexpr int HX = 16 / ES;    // x halo: one aligned 16-byte group
+    // bytes of one component in each box kind
     static constexpr int CTR_BYTES = TX * TY * TZ * ES;
     static constexpr int HX_BYTES = HX * TY * TZ * ES;
     static constexpr int HY_BYTES = TX * TZ * ES;
     static constexpr int HZ_BYTES = TX * TY * ES;
-    static constexpr int CTR = pad128(CTR_BYTES);
-    static constexpr int HXO = CTR;                        // offsets inside a source slot
-    static constexpr int HYO = HXO + pad128(HX_BYTES);
-    static constexpr int HZO = HYO + pad128(HY_BYTES);
-    static constexpr int SRC = HZO + pad128(HZ_BYTES);
-    static constexpr int SRC_TX = CTR_BYTES + HX_BYTES + HY_BYTES + HZ_BYTES;  // bytes per source
-    static constexpr int TGT0 = SLOTS * SRC;               // target slots after the source slots
-    static constexpr int BUF = TGT0 + SLOTS * CTR;
+    // one TMA box carries NL consecutive components of a run; regions per type t:
+    static constexpr int R_CTR = pad128(NL * CTR_BYTES);
+    static constexpr int R_HX = pad128(NL * HX_BYTES);
+    static constexpr int R_HY = pad128(NL * HY_BYTES);
+    static constexpr int R_HZ = pad128(NL * HZ_BYTES);
+    static constexpr int SRC_T = R_CTR + R_HX + R_HY + R_HZ;   // source regions of one type
+    static constexpr int HXO = R_CTR, HYO = R_CTR + R_HX, HZO = R_CTR + R_HX + R_HY;
+    static constexpr int TGT0 = 2 * SRC_T;                       // target regions after the sources
+    static constexpr int BUF = TGT0 + 2 * R_CTR;
+    static constexpr int SRC_TX = NL * (CTR_BYTES + HX_BYTES + HY_BYTES + HZ_BYTES);  // per run
+    static constexpr int TGT_TX = NL * CTR_BYTES;
     static constexpr int COEF = pad128(class_size(N, B) * CPAD * 4);
-    static constexpr int BYTES = COEF + 2 * BUF + 128;     // table, two buffers, mbarriers
+    static constexpr int BYTES = COEF + 2 * BUF + 128 + 128;  // table, two buffers, mbarriers,
+                                                              // and slack to align the base to 128 B
     static_assert(TX % HX == 0, "tile width must be a multiple of the 16-byte group");
+    static_assert(CTR_BYTES % 16 == 0 && HX_BYTES % 16 == 0 && HY_BYTES % 16 == 0 && HZ_BYTES % 16 == 0,
+                  "box components must stay 16-byte aligned");
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -132,11 +138,27 @@ __device__ __forceinline__ float lds(const unsigned char* base, int byte_off) {
 
 // Optional self-checks (compile with -DRTPN_STAGE_CHECKS): an index or alignment that breaks the
 // layout sets STATUS_CHECK and the access is skipped.
+// With the checks on, status[1..] is a diagnostic record: [1] id of the first failed check,
+// [2] a value of it, [3] issue() calls, [4] successful waits, [5] stage of a timeout + 1,
+// [6] copies issued.
 #ifdef RTPN_STAGE_CHECKS
-#define RTPN_SCHECK(cond) ((cond) ? true : (atomicOr(a.status, STATUS_CHECK), false))
+__device__ __forceinline__ bool scheck_fail(unsigned* st, unsigned id, unsigned val, unsigned aux) {
+    atomicOr(st, STATUS_CHECK);
+    if (atomicCAS(st + 1, 0u, id) == 0u) {  // the first failure keeps its details
+        st[2] = val;
+        st[7] = aux;
+    }
+    return false;
+}
+#define RTPN_SCHECK_AUX(cond, id, val, aux) ((cond) ? true : scheck_fail(a.status, (id), (unsigned)(val), (unsigned)(aux)))
+#define RTPN_SCHECK_ID(cond, id, val) RTPN_SCHECK_AUX(cond, id, val, blockIdx.x)
+#define RTPN_SCOUNT(slot) atomicAdd(a.status + (slot), 1u)
 #else
-#define RTPN_SCHECK(cond) true
+#define RTPN_SCHECK_AUX(cond, id, val, aux) true
+#define RTPN_SCHECK_ID(cond, id, val) true
+#define RTPN_SCOUNT(slot) ((void)0)
 #endif
+#define RTPN_SCHECK(cond) RTPN_SCHECK_ID(cond, __LINE__, 0)
 
 // Tile geometry: origin, valid extents and halo coordinates ([axis][side], side 1 = upper).
 struct TileGeo {
@@ -181,11 +203,16 @@ __device__ __forceinline__ TileGeo tile_geo(const Args& a, long long t) {
 // Source x slot: 1 (read at i+1 by its partners) iff (M even) == (cos type); z slot: 1 iff l+M even.
 __device__ __forceinline__ int dir_x(int M, int t) { return ((M & 1) == 0) == (t == 0) ? 1 : -1; }
 
-template <int N, int A, typename S, int TX, int TY, int TZ>
+// SPLIT threads share a cell: part p owns the targets with l/2 in [p NLP, (p+1) NLP) and sweeps the
+// sources that reach them (its range and one neighbouring l on each side), so each thread keeps a
+// window of 3 x 2 x NLP accumulators and the CTA runs SPLIT times as many warps on the same tile.
+template <int N, int A, typename S, int TX, int TY, int TZ, int SPLIT>
 __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* smem) {
     using L = Layout<N, A, S, TX, TY, TZ>;
     constexpr int B = 1 - A;
     constexpr int NL = L::NL;
+    constexpr int CELLS = TX * TY * TZ;
+    constexpr int NLP = (NL + SPLIT - 1) / SPLIT;
     constexpr int HX = L::HX;
     constexpr int NSTAGE = N + 2;  // stage i: sources of column i (i <= N), targets of column i-1
     const int cA0 = A == 0 ? 0 : class_size(N, 0);
@@ -194,9 +221,13 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     const int* colB = a.colstart + B * (N + 2);
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+    const int part = tid / CELLS, ctid = tid % CELLS;
+    const int lx = ctid % TX, ly = (ctid / TX) % TY, lz = ctid / (TX * TY);
     const long long V = a.V;
 
+    // TMA writes into shared memory need 128-byte aligned destinations; the dynamic shared memory
+    // window is not guaranteed to start on one, so the layout starts at the next 128-byte boundary.
+    smem += (128u - (smem_addr(smem) & 127u)) & 127u;
     float* coef = reinterpret_cast<float*>(smem);
     unsigned char* bufs = smem + L::COEF;
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(bufs + 2 * L::BUF);
@@ -208,12 +239,19 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     const CUtensorMap* map_hz = a.maps + 3;
 
     // coupling constants into shared memory
-    for (int i = tid; i < class_size(N, B) * CPAD; i += TX * TY * TZ) coef[i] = a.coef[i];
+    for (int i = tid; i < class_size(N, B) * CPAD; i += CELLS * SPLIT) coef[i] = a.coef[i];
     if (tid < 4) {
         // the maps were written by the host before the launch; make them visible to the async proxy
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(a.maps + tid)
                      : "memory");
     }
+#ifdef RTPN_STAGE_CHECKS
+    if (tid == 0) {
+        RTPN_SCHECK_AUX(a.nc == (N + 1) * (N + 1), 121, a.nc, 0);
+        RTPN_SCHECK_AUX(colA[0] == 0 && colA[N + 1] == class_size(N, A), 122, colA[N + 1], colA[1]);
+        RTPN_SCHECK_AUX(colB[0] == 0 && colB[N + 1] == class_size(N, B), 123, colB[N + 1], colB[1]);
+    }
+#endif
     if (tid == 0) {
         mbar_init(bar0, 1);
         mbar_init(bar1, 1);
@@ -225,7 +263,10 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     const long long my_tiles = a.tiles > blockIdx.x ? (a.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const long long total = my_tiles * NSTAGE;
 
-    // Issue global stage s (tile s / NSTAGE of this CTA, column stage s % NSTAGE): warp 0.
+    // Issue global stage s (tile s / NSTAGE of this CTA, column stage s % NSTAGE): warp 0.  One TMA
+    // box per (type, box kind) carries the NL consecutive components of a (type, |m|) run starting
+    // at the run's first component: lanes 0-3 the source boxes of type 0, 4-7 of type 1, 8-9 the
+    // target boxes of types 0 and 1.
     auto issue = [&](long long s) {
         if (s == a.skip_stage) return;
         const long long ti = blockIdx.x + (s / NSTAGE) * (long long)gridDim.x;
@@ -233,47 +274,52 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
         const TileGeo g = tile_geo<TX, TY, TZ, HX>(a, ti);
         unsigned char* buf = bufs + (s & 1) * L::BUF;
         const unsigned bar = (s & 1) ? bar1 : bar0;
-        const int nsrc = i <= N ? ntypes(i) * column_len(N, i, B) : 0;
-        const int ntgt = i >= 1 ? ntypes(i - 1) * column_len(N, i - 1, A) : 0;
-        if (lane == 0) mbar_expect_tx(bar, nsrc * L::SRC_TX + ntgt * L::CTR_BYTES);
+        const bool src_t[2] = {i <= N && column_len(N, i, B) > 0, i >= 1 && i <= N && column_len(N, i, B) > 0};
+        const int M = i - 1;
+        const bool tgt_t[2] = {M >= 0 && column_len(N, M, A) > 0, M >= 1 && column_len(N, M, A) > 0};
+        const unsigned bytes = (src_t[0] + src_t[1]) * L::SRC_TX + (tgt_t[0] + tgt_t[1]) * L::TGT_TX;
+        if (lane == 0) {
+            mbar_expect_tx(bar, bytes);
+            RTPN_SCOUNT(3);
+        }
         __syncwarp();
-        for (int j = lane; j < 2 * L::SLOTS; j += 32) {
-            if (j < L::SLOTS) {  // source slot j = t * NL + l/2 of column i
-                const int t = j / NL, l = 2 * (j % NL) + B;
-                if (i > N || l < i || l > N || (t == 1 && i == 0)) continue;
-                const int c = cB0 + colB[i] + t * column_len(N, i, B) + (l - first_l(i, B)) / 2;
-                const unsigned d = smem_addr(buf + j * L::SRC);
-                const int sx = dir_x(i, t) > 0 ? 1 : 0;
-                const int sy = t == 0 ? 1 : 0;
-                const int sz = ((l + i) & 1) == 0 ? 1 : 0;
-                const int hxs = sx ? g.hx_start[1] : g.hx_start[0];
-                if (!RTPN_SCHECK(c >= 0 && c < a.nc && g.x0 % HX == 0 && hxs % HX == 0 &&
-                                 j * L::SRC + L::SRC <= L::TGT0 && (d & 127) == 0))
-                    continue;
+        if (lane < 8) {
+            const int t = lane / 4, kind = lane % 4;
+            if (!src_t[t]) return;
+            const int c = cB0 + colB[i] + t * column_len(N, i, B);  // first component of the run
+            const unsigned d = smem_addr(buf + t * L::SRC_T);
+            if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 101, c)) return;
+            if (!RTPN_SCHECK_ID((d & 127) == 0, 103, d)) return;
+            RTPN_SCOUNT(6);
+            if (kind == 0) {
                 tma_load_4d(d, map_ctr, g.x0, g.y0, g.z0, c, bar);
+            } else if (kind == 1) {  // x slot 1 -> partners read i+1 (upper halo)
+                const int hxs = dir_x(i, t) > 0 ? g.hx_start[1] : g.hx_start[0];
+                if (!RTPN_SCHECK_ID(hxs % HX == 0, 102, hxs)) return;
                 tma_load_4d(d + L::HXO, map_hx, hxs, g.y0, g.z0, c, bar);
-                tma_load_4d(d + L::HYO, map_hy, g.x0, sy ? g.hc[1][1] : g.hc[1][0], g.z0, c, bar);
-                tma_load_4d(d + L::HZO, map_hz, g.x0, g.y0, sz ? g.hc[2][1] : g.hc[2][0], c, bar);
-            } else {  // target slot of column i - 1
-                const int jj = j - L::SLOTS;
-                const int M = i - 1;
-                const int t = jj / NL, l = 2 * (jj % NL) + A;
-                if (M < 0 || l < M || l > N || (t == 1 && M == 0)) continue;
-                const int c = cA0 + colA[M] + t * column_len(N, M, A) + (l - first_l(M, A)) / 2;
-                const unsigned d = smem_addr(buf + L::TGT0 + jj * L::CTR);
-                if (!RTPN_SCHECK(c >= 0 && c < a.nc && g.x0 % HX == 0 &&
-                                 L::TGT0 + jj * L::CTR + L::CTR <= L::BUF && (d & 127) == 0))
-                    continue;
-                tma_load_4d(d, map_ctr, g.x0, g.y0, g.z0, c, bar);
+            } else if (kind == 2) {  // cos type reads y+1, sin type y-1
+                tma_load_4d(d + L::HYO, map_hy, g.x0, t == 0 ? g.hc[1][1] : g.hc[1][0], g.z0, c, bar);
+            } else {                 // z slot 1 (l + M even) reads z+1
+                tma_load_4d(d + L::HZO, map_hz, g.x0, g.y0, ((B + i) & 1) == 0 ? g.hc[2][1] : g.hc[2][0], c,
+                            bar);
             }
+        } else if (lane < 10) {
+            const int t = lane - 8;
+            if (!tgt_t[t]) return;
+            const int c = cA0 + colA[M] + t * column_len(N, M, A);
+            const unsigned d = smem_addr(buf + L::TGT0 + t * L::R_CTR);
+            if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 111, c)) return;
+            if (!RTPN_SCHECK_ID((d & 127) == 0, 113, d)) return;
+            RTPN_SCOUNT(6);
+            tma_load_4d(d, map_ctr, g.x0, g.y0, g.z0, c, bar);
         }
     };
 
-    float prev[2][NL], cur[2][NL], next[2][NL];
+    float prev[2][NLP], cur[2][NLP], next[2][NLP];
 #pragma unroll
     for (int t = 0; t < 2; ++t)
 #pragma unroll
-        for (int q = 0; q < NL; ++q) prev[t][q] = cur[t][q] = next[t][q] = 0.f;
+        for (int q = 0; q < NLP; ++q) prev[t][q] = cur[t][q] = next[t][q] = 0.f;
 
     if (tid < 32 && total > 0) issue(0);
     long long fail_at = -1;
@@ -283,7 +329,8 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     long long cell = 0;
     float al[8], be[8];
     float al0 = 0.f, be0 = 0.f, ga0 = 0.f;
-    int my = 0, offy[2] = {0, 0};
+    int my = 0;
+    bool iny[2] = {true, true};
 
     for (long long s = 0; s < total; ++s) {
         const int i = (int)(s % NSTAGE);
@@ -295,8 +342,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
 #pragma unroll
             for (int t = 0; t < 2; ++t) {  // y slot is fixed per type: cos reads y+1, sin y-1
                 const int dy = t == 0 ? 1 : -1;
-                offy[t] = (ly + dy >= 0 && ly + dy < g.wy) ? my + dy * TX * L::ES
-                                                         : L::HYO + (lz * TX + lx) * L::ES;
+                iny[t] = ly + dy >= 0 && ly + dy < g.wy;
             }
 #pragma unroll
             for (int k = 0; k < 8; ++k) al[k] = be[k] = 0.f;
@@ -320,8 +366,12 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
         const bool ok = wait_phase(bar, (unsigned)((s >> 1) & 1), a.wait_limit);
         if (__syncthreads_or(!ok)) {
             fail_at = s;
+#ifdef RTPN_STAGE_CHECKS
+            if (tid == 0) atomicCAS(a.status + 5, 0u, (unsigned)(s + 1));
+#endif
             break;
         }
+        if (tid == 0) RTPN_SCOUNT(4);
         if (tid < 32 && s + 1 < total) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(s + 1);
@@ -332,46 +382,64 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
             // ---- scatter source column i into prev (i-1), cur (i), next (i+1)
             const int Ms = i;
             const int dz = ((B + Ms) & 1) == 0 ? 1 : -1;
-            const int offz = (lz + dz >= 0 && lz + dz < g.wz) ? my + dz * TX * TY * L::ES
-                                                              : L::HZO + (ly * TX + lx) * L::ES;
+            const bool inz = lz + dz >= 0 && lz + dz < g.wz;
+            const int fq = first_l(Ms, B) / 2;  // component q' = q - fq inside a run's boxes
             static_for<2>([&](auto ti) {
                 constexpr int ts = decltype(ti)::value;
                 if (ts == 1 && Ms == 0) return;
+                const unsigned char* rb = buf + ts * L::SRC_T;
                 const int dx = dir_x(Ms, ts);
-                const int offx = (lx + dx >= 0 && lx + dx < g.wx)
-                                     ? my + dx * L::ES
-                                     : L::HXO + ((lz * TY + ly) * HX + (dx > 0 ? g.hx_elem[1] : g.hx_elem[0])) * L::ES;
+                const bool inx = lx + dx >= 0 && lx + dx < g.wx;
+                constexpr int dy = ts == 0 ? 1 : -1;
+                // per neighbour: address of component q' = 0 and the stride between components
+                const unsigned char* pc = rb + my - fq * L::CTR_BYTES;
+                const unsigned char* px =
+                    inx ? pc + dx * L::ES
+                        : rb + L::HXO + ((lz * TY + ly) * HX + (dx > 0 ? g.hx_elem[1] : g.hx_elem[0])) * L::ES -
+                              fq * L::HX_BYTES;
+                const int sx = inx ? L::CTR_BYTES : L::HX_BYTES;
+                const unsigned char* py =
+                    iny[ts] ? pc + dy * TX * L::ES : rb + L::HYO + (lz * TX + lx) * L::ES - fq * L::HY_BYTES;
+                const int sy = iny[ts] ? L::CTR_BYTES : L::HY_BYTES;
+                const unsigned char* pz =
+                    inz ? pc + dz * TX * TY * L::ES : rb + L::HZO + (ly * TX + lx) * L::ES - fq * L::HZ_BYTES;
+                const int sz = inz ? L::CTR_BYTES : L::HZ_BYTES;
                 // local index of slot (ts, q) is cbase + q
-                const int cbase = colB[Ms] + ts * column_len(N, Ms, B) - first_l(Ms, B) / 2;
+                const int cbase = colB[Ms] + ts * column_len(N, Ms, B) - fq;
+                static_for<SPLIT>([&](auto pi) {
+                constexpr int P = decltype(pi)::value;
+                constexpr int QLO = P * NLP, QHI = (P + 1) * NLP < NL ? (P + 1) * NLP : NL;
+                if (part != P) return;
                 static_for<NL>([&](auto qi) {
                     constexpr int q = decltype(qi)::value;
                     constexpr int ls = 2 * q + B;
-                    if constexpr (ls <= N) {
+                    constexpr int lm = (ls - 1) / 2, lp = (ls + 1) / 2;  // acc index of l-1, l+1
+                    constexpr bool has_m = ls - 1 >= 0 && lm >= QLO && lm < QHI;
+                    constexpr bool has_p = ls + 1 <= N && lp >= QLO && lp < QHI;
+                    if constexpr (ls <= N && (has_m || has_p)) {
                         if (ls < Ms) return;
-                        const unsigned char* base = buf + (ts * NL + q) * L::SRC;
-                        if (!RTPN_SCHECK(offx >= 0 && offx < L::SRC && offy[ts] >= 0 && offy[ts] < L::SRC &&
-                                         offz >= 0 && offz < L::SRC && my < L::CTR_BYTES &&
-                                         cbase + q >= 0 && cbase + q < class_size(N, B)))
+                        if (!RTPN_SCHECK(q - fq >= 0 && q - fq < NL && cbase + q >= 0 &&
+                                         cbase + q < class_size(N, B)))
                             return;
-                        const float c = lds<S>(base, my);
-                        const float ddx = lds<S>(base, offx) - c;
-                        const float ddy = lds<S>(base, offy[ts]) - c;
-                        const float ddz = lds<S>(base, offz) - c;
+                        const float c = lds<S>(pc, q * L::CTR_BYTES);
+                        const float ddx = lds<S>(px, q * sx) - c;
+                        const float ddy = lds<S>(py, q * sy) - c;
+                        const float ddz = lds<S>(pz, q * sz) - c;
                         const float4* cf = reinterpret_cast<const float4*>(coef + (cbase + q) * CPAD);
                         const float4 k0 = cf[0], k1 = cf[1], k2 = cf[2];
-                        constexpr int lm = (ls - 1) / 2, lp = (ls + 1) / 2;  // acc index of l-1, l+1
-                        constexpr bool has_m = ls - 1 >= 0, has_p = ls + 1 <= N;
-                        if constexpr (has_m) cur[ts][lm] = fmaf(k0.x, ddz, cur[ts][lm]);
-                        if constexpr (has_p) cur[ts][lp] = fmaf(k0.y, ddz, cur[ts][lp]);
-                        if constexpr (has_m) prev[ts][lm] = fmaf(k0.z, ddx, prev[ts][lm]);
-                        if constexpr (has_p) prev[ts][lp] = fmaf(k0.w, ddx, prev[ts][lp]);
-                        if constexpr (has_m) next[ts][lm] = fmaf(k1.x, ddx, next[ts][lm]);
-                        if constexpr (has_p) next[ts][lp] = fmaf(k1.y, ddx, next[ts][lp]);
-                        if constexpr (has_m) prev[1 - ts][lm] = fmaf(k1.z, ddy, prev[1 - ts][lm]);
-                        if constexpr (has_p) prev[1 - ts][lp] = fmaf(k1.w, ddy, prev[1 - ts][lp]);
-                        if constexpr (has_m) next[1 - ts][lm] = fmaf(k2.x, ddy, next[1 - ts][lm]);
-                        if constexpr (has_p) next[1 - ts][lp] = fmaf(k2.y, ddy, next[1 - ts][lp]);
+                        constexpr int am = has_m ? lm - QLO : 0, ap = has_p ? lp - QLO : 0;
+                        if constexpr (has_m) cur[ts][am] = fmaf(k0.x, ddz, cur[ts][am]);
+                        if constexpr (has_p) cur[ts][ap] = fmaf(k0.y, ddz, cur[ts][ap]);
+                        if constexpr (has_m) prev[ts][am] = fmaf(k0.z, ddx, prev[ts][am]);
+                        if constexpr (has_p) prev[ts][ap] = fmaf(k0.w, ddx, prev[ts][ap]);
+                        if constexpr (has_m) next[ts][am] = fmaf(k1.x, ddx, next[ts][am]);
+                        if constexpr (has_p) next[ts][ap] = fmaf(k1.y, ddx, next[ts][ap]);
+                        if constexpr (has_m) prev[1 - ts][am] = fmaf(k1.z, ddy, prev[1 - ts][am]);
+                        if constexpr (has_p) prev[1 - ts][ap] = fmaf(k1.w, ddy, prev[1 - ts][ap]);
+                        if constexpr (has_m) next[1 - ts][am] = fmaf(k2.x, ddy, next[1 - ts][am]);
+                        if constexpr (has_p) next[1 - ts][ap] = fmaf(k2.y, ddy, next[1 - ts][ap]);
                     }
+                });
                 });
             });
         }
@@ -395,16 +463,21 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                 S* tptr = reinterpret_cast<S*>(a.u) +
                           (long long)(cA0 + colA[M] + t * column_len(N, M, A) - first_l(M, A) / 2) * V +
                           cell;
+                static_for<SPLIT>([&](auto pi) {
+                constexpr int P = decltype(pi)::value;
+                constexpr int QLO = P * NLP, QHI = (P + 1) * NLP < NL ? (P + 1) * NLP : NL;
+                if (part != P) return;
                 static_for<NL>([&](auto qi) {
                     constexpr int q = decltype(qi)::value;
                     constexpr int l = 2 * q + A;
-                    if constexpr (l <= N) {
+                    if constexpr (l <= N && q >= QLO && q < QHI) {
                         if (l < M) return;
                         const long long gi = (long long)(cA0 + colA[M] + t * column_len(N, M, A) -
                                                          first_l(M, A) / 2 + q);
                         if (!RTPN_SCHECK(gi >= cA0 && gi < a.nc && cell >= 0 && cell < V)) return;
-                        const float old = lds<S>(buf + L::TGT0 + (t * NL + q) * L::CTR, my);
-                        const float r = prev[t][q];
+                        const float old =
+                            lds<S>(buf + L::TGT0 + t * L::R_CTR, my + (q - first_l(M, A) / 2) * L::CTR_BYTES);
+                        const float r = prev[t][q - QLO];
                         float nv;
                         if (A == 0 && l == 0 && M == 0)
                             nv = fmaf(al0, old, fmaf(-be0, r, ga0));
@@ -413,13 +486,14 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                         win::store<S>(tptr + (long long)q * V, nv);
                     }
                 });
+                });
             });
         }
         // shift the window: prev <- cur <- next <- 0 (also resets a finished tile)
 #pragma unroll
         for (int t = 0; t < 2; ++t)
 #pragma unroll
-            for (int q = 0; q < NL; ++q) {
+            for (int q = 0; q < NLP; ++q) {
                 prev[t][q] = cur[t][q];
                 cur[t][q] = next[t][q];
                 next[t][q] = 0.f;
@@ -428,7 +502,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
 #pragma unroll
             for (int t = 0; t < 2; ++t)
 #pragma unroll
-                for (int q = 0; q < NL; ++q) prev[t][q] = cur[t][q] = 0.f;
+                for (int q = 0; q < NLP; ++q) prev[t][q] = cur[t][q] = 0.f;
         }
         __syncthreads();  // buffer s & 1 may be refilled by stage s + 2
     }

@@ -14,13 +14,17 @@
 namespace rtpn {
 namespace win {
 
+// Internal linkage for everything but the uniquely named entry points: every variant of this file
+// defines a kernel of the same name, and the linker must not merge them.
+namespace {
+
 constexpr int kN = RTPN_WN;
 constexpr int kA = RTPN_WCLS;
 constexpr int kSources = class_size(kN, 1 - kA);
 static_assert(kSources * 10 * 4 <= 64 * 1024 - 1024, "coefficient table exceeds constant memory");
 
-// coefficient of source j (class 1 - kA, local index) for relation k: M_d[a][b] * dir / h
-static __constant__ float c_coef[kSources * 10];
+// coefficient of source j (class 1 - kA, local index) for relation k: M_d[a][b] * dir
+__constant__ float c_coef[kSources * 10];
 
 template <typename S>
 __global__ void __launch_bounds__(256) k_window(Args a) {
@@ -28,6 +32,8 @@ __global__ void __launch_bounds__(256) k_window(Args a) {
     if (!cell_of(a, blockIdx.x, threadIdx.x, &x, &y, &z)) return;
     substep_cell<kN, kA, S>(a, c_coef, x, y, z);
 }
+
+}  // namespace
 
 int RTPN_VARIANT(window_upload)(const float* host, int count) {
     if (count != kSources * 10) return (int)cudaErrorInvalidValue;
