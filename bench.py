@@ -65,6 +65,24 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# DRAM bytes per cell of one launch of the dominant kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of a smaller grid with the same tile, scaled by the
+# cell count; valid only for the kernel build and configuration it was taken on.
+# key: (kernel, N, storage, tile, threads per cell, target class)
+NCU_TRAFFIC = {
+    ("stage", 39, "fp32", (40, 2, 2), 2, 1): {
+        "bytes_per_cell": (6.309185e9 + 1.659710e9) / 80 ** 3,
+        "source": "profiles/stage_p39_200.md: P39 80^3 capture of the odd-class pass, scaled to the grid"},
+}
+
+
+def traffic_per_launch(kernel, N, storage, tile, chunks, cls, cells):
+    t = NCU_TRAFFIC.get((kernel, N, storage, tuple(tile), chunks, cls))
+    if t is None:
+        return None, None
+    return t["bytes_per_cell"] * cells, t["source"]
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -222,10 +240,13 @@ def main():
     dom = max(per_pass, key=lambda c: per_pass[c])
     hbm, peak_kind = peaks()
     achieved = alg[dom] / (per_pass[dom] / 1e3) / 1e9
+    kname = {1: "generic", 2: "window", 3: "stage"}.get(ctx.info().kernel, "?")
+    traffic, traffic_src = traffic_per_launch(kname, args.N, args.precision, tuple(ctx.info().tile),
+                                              ctx.info().chunks, dom, V)
     step_ms = ms / args.steps
     step_bytes = V * (info.n_c * 2 * s + 12)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_src,
                 "kernel": f"substep pass ({'even' if dom == 0 else 'odd'} class)",
                 "peak_kind": peak_kind,
                 "pass_ms": {"even": per_pass[0], "odd": per_pass[1]},

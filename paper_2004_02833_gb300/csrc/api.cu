@@ -287,8 +287,9 @@ void release(rtpn_ctx* ctx) {
     ctx->own = nullptr;
 }
 
-// The staged kernel joins automatic selection once it has passed its GPU tests.
-constexpr bool kStageInAuto = false;
+// Automatic selection: the staged kernel where it is compiled for (N, precision) and nx gives
+// 16-byte rows, else the register-window kernel, else the generic one.
+constexpr bool kStageInAuto = true;
 
 int choose_kernel(rtpn_ctx* ctx) {
     int k = ctx->kernel;
