@@ -184,6 +184,8 @@ int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long
     a.nty = (a.ny + v.ty - 1) / v.ty;
     a.ntz = (a.nz + v.tz - 1) / v.tz;
     a.tiles = (long long)a.ntx * a.nty * a.ntz;
+    // the kernel counts tiles and per-CTA stages in 32 bits
+    if (a.tiles * (ctx->N + 2) >= (1ll << 31)) return (int)cudaErrorInvalidValue;
     a.maps = (const CUtensorMap*)ctx->stage_maps_dev;
     a.nc = ctx->md.nc;
     a.status = ctx->status;

@@ -167,13 +167,15 @@ struct TileGeo {
     int hx_start[2], hx_elem[2];
 };
 
+// Tile t (t < 2^31, checked on the host) of the walk: z fastest, then x, then y.  32-bit division:
+// this runs once per tile and thread.
 template <int TX, int TY, int TZ, int HX>
-__device__ __forceinline__ TileGeo tile_geo(const Args& a, long long t) {
+__device__ __forceinline__ TileGeo tile_geo(const Args& a, unsigned t) {
     TileGeo g;
-    const long long bz = t % a.ntz;
-    const long long rest = t / a.ntz;
-    g.x0 = (int)(rest % a.ntx) * TX;
-    g.y0 = (int)(rest / a.ntx) * TY;
+    const unsigned bz = t % (unsigned)a.ntz;
+    const unsigned rest = t / (unsigned)a.ntz;
+    g.x0 = (int)(rest % (unsigned)a.ntx) * TX;
+    g.y0 = (int)(rest / (unsigned)a.ntx) * TY;
     g.z0 = (int)bz * TZ;
     g.wx = min(TX, a.nx - g.x0);
     g.wy = min(TY, a.ny - g.y0);
@@ -260,18 +262,16 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     }
     __syncthreads();
 
-    const long long my_tiles = a.tiles > blockIdx.x ? (a.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const long long total = my_tiles * NSTAGE;
+    // stages of this CTA (the host keeps tiles * NSTAGE below 2^31)
+    const int my_tiles = a.tiles > blockIdx.x ? (int)((a.tiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+    const int total = my_tiles * NSTAGE;
 
-    // Issue global stage s (tile s / NSTAGE of this CTA, column stage s % NSTAGE): warp 0.  One TMA
-    // box per (type, box kind) carries the NL consecutive components of a (type, |m|) run starting
-    // at the run's first component: lanes 0-3 the source boxes of type 0, 4-7 of type 1, 8-9 the
-    // target boxes of types 0 and 1.
-    auto issue = [&](long long s) {
+    // Issue stage s of this CTA (column stage i of the tile with geometry g): warp 0.  One TMA box
+    // per (type, box kind) carries the NL consecutive components of a (type, |m|) run starting at
+    // the run's first component: lanes 0-3 the source boxes of type 0, 4-7 of type 1, 8-9 the target
+    // boxes of types 0 and 1.
+    auto issue = [&](int s, int i, const TileGeo& g) {
         if (s == a.skip_stage) return;
-        const long long ti = blockIdx.x + (s / NSTAGE) * (long long)gridDim.x;
-        const int i = (int)(s % NSTAGE);
-        const TileGeo g = tile_geo<TX, TY, TZ, HX>(a, ti);
         unsigned char* buf = bufs + (s & 1) * L::BUF;
         const unsigned bar = (s & 1) ? bar1 : bar0;
         const bool src_t[2] = {i <= N && column_len(N, i, B) > 0, i >= 1 && i <= N && column_len(N, i, B) > 0};
@@ -321,10 +321,13 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
 #pragma unroll
         for (int q = 0; q < NLP; ++q) prev[t][q] = cur[t][q] = next[t][q] = 0.f;
 
-    if (tid < 32 && total > 0) issue(0);
-    long long fail_at = -1;
+    // geometry of the current tile, computed once per tile (and by warp 0 once more for the first
+    // issue into the next tile)
+    unsigned cur_tile = blockIdx.x;
+    TileGeo g = tile_geo<TX, TY, TZ, HX>(a, cur_tile);
+    if (tid < 32 && total > 0) issue(0, 0, g);
+    int fail_at = -1;
 
-    TileGeo g{};
     bool active = false;
     long long cell = 0;
     float al[8], be[8];
@@ -332,10 +335,12 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     int my = 0;
     bool iny[2] = {true, true};
 
-    for (long long s = 0; s < total; ++s) {
-        const int i = (int)(s % NSTAGE);
+    for (int s = 0, i = 0; s < total; ++s, i = (i == NSTAGE - 1) ? 0 : i + 1) {
         if (i == 0) {  // new tile: geometry, factors, fixed neighbour offsets
-            g = tile_geo<TX, TY, TZ, HX>(a, blockIdx.x + (s / NSTAGE) * (long long)gridDim.x);
+            if (s > 0) {
+                cur_tile += gridDim.x;
+                g = tile_geo<TX, TY, TZ, HX>(a, cur_tile);
+            }
             active = lx < g.wx && ly < g.wy && lz < g.wz;
             cell = ((long long)(g.z0 + lz) * a.ny + (g.y0 + ly)) * a.nx + (g.x0 + lx);
             my = ((lz * TY + ly) * TX + lx) * L::ES;
@@ -374,7 +379,12 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
         if (tid == 0) RTPN_SCOUNT(4);
         if (tid < 32 && s + 1 < total) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(s + 1);
+            if (i + 1 < NSTAGE) {
+                issue(s + 1, i + 1, g);
+            } else {
+                const TileGeo gn = tile_geo<TX, TY, TZ, HX>(a, cur_tile + gridDim.x);
+                issue(s + 1, 0, gn);
+            }
         }
         const unsigned char* buf = bufs + (s & 1) * L::BUF;
 
@@ -504,7 +514,8 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
 #pragma unroll
                 for (int q = 0; q < NLP; ++q) prev[t][q] = cur[t][q] = 0.f;
         }
-        __syncthreads();  // buffer s & 1 may be refilled by stage s + 2
+        // No barrier here: buffer s & 1 is refilled by the issue of stage s + 2, which warp 0 makes
+        // only after the barrier of stage s + 1's wait, when every thread is done with stage s.
     }
 
     if (fail_at >= 0) {
