@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     p.add_argument("--kernel", default="auto", choices=["auto", "generic", "window", "stage"])
     p.add_argument("--tile", default="0,0,0")
-    p.add_argument("--chunks", type=int, default=0, help="threads per cell of the staged kernel")
+    p.add_argument("--depth", type=int, default=0, help="stage buffers of the staged kernel (0 = default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true",
@@ -68,16 +68,13 @@ def peaks():
 # DRAM bytes per cell of one launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a smaller grid with the same tile, scaled by the
 # cell count; valid only for the kernel build and configuration it was taken on.
-# key: (kernel, N, storage, tile, threads per cell, target class)
+# key: (kernel, N, storage, tile, stage depth, target class)
 NCU_TRAFFIC = {
-    ("stage", 39, "fp32", (40, 2, 2), 2, 1): {
-        "bytes_per_cell": (6.309185e9 + 1.659710e9) / 80 ** 3,
-        "source": "profiles/stage_p39_200.md: P39 80^3 capture of the odd-class pass, scaled to the grid"},
 }
 
 
-def traffic_per_launch(kernel, N, storage, tile, chunks, cls, cells):
-    t = NCU_TRAFFIC.get((kernel, N, storage, tuple(tile), chunks, cls))
+def traffic_per_launch(kernel, N, storage, tile, depth, cls, cells):
+    t = NCU_TRAFFIC.get((kernel, N, storage, tuple(tile), depth, cls))
     if t is None:
         return None, None
     return t["bytes_per_cell"] * cells, t["source"]
@@ -198,8 +195,8 @@ def main():
     stream = torch.cuda.Stream()
     ctx = rtpn.Context(args.N, inst.shape, inst.h, inst.bc, args.precision, inst.dt)
     ctx.set_stream(stream)
-    if args.kernel != "auto" or any(tile) or args.chunks:
-        ctx.set_kernel(args.kernel, tile, args.chunks)
+    if args.kernel != "auto" or any(tile) or args.depth:
+        ctx.set_kernel(args.kernel, tile, args.depth)
     info = ctx.info()
     with torch.cuda.stream(stream):
         media = [torch.tensor(a, dtype=torch.float32, device="cuda")
@@ -242,7 +239,7 @@ def main():
     achieved = alg[dom] / (per_pass[dom] / 1e3) / 1e9
     kname = {1: "generic", 2: "window", 3: "stage"}.get(ctx.info().kernel, "?")
     traffic, traffic_src = traffic_per_launch(kname, args.N, args.precision, tuple(ctx.info().tile),
-                                              ctx.info().chunks, dom, V)
+                                              ctx.info().depth, dom, V)
     step_ms = ms / args.steps
     step_bytes = V * (info.n_c * 2 * s + 12)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -274,7 +271,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": 2 * args.steps + 1, "nonfinite": nonfinite, "forms": forms,
             "kernel_used": {1: "generic", 2: "window", 3: "stage"}.get(ctx.info().kernel, "?"),
-            "tile": list(ctx.info().tile), "chunks": ctx.info().chunks}
+            "tile": list(ctx.info().tile), "depth": ctx.info().depth}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

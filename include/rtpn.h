@@ -83,7 +83,7 @@ typedef struct rtpn_info {
     size_t factor_bytes;   /* device bytes of the per-cell substep factors   */
     long long steps_done;  /* full steps taken since the last set_moments    */
     int tile[3];           /* CTA tile of the active kernel (0 = not tiled)  */
-    int chunks;            /* threads per cell (component chunks)            */
+    int depth;             /* stage buffers of the staged kernel (1 = other) */
 } rtpn_info;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -133,10 +133,12 @@ int rtpn_set_stream(rtpn_ctx* ctx, void* stream);
  * then stays. */
 int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z);
 
-/* As rtpn_set_kernel, and for RTPN_KERNEL_STAGE the number of threads that share a cell, each
- * owning a contiguous range of l (component chunks of the register window); 0 = any compiled.
- * RTPN_EUNSUPPORTED if no staged variant is compiled for (N, tile, chunks). */
-int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z, int chunks);
+/* As rtpn_set_kernel, and for RTPN_KERNEL_STAGE the pipeline depth: the number of shared-memory
+ * stage buffers, of which all but one hold copies in flight (2..8; 0 = any compiled).  The staged
+ * kernel runs two threads per cell of the tile (one per target type) plus one producer warp.
+ * RTPN_EINVAL for a depth outside 0..8, RTPN_EUNSUPPORTED if no staged variant is compiled for
+ * (N, tile, depth). */
+int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z, int depth);
 
 /*
  * Media: per-cell sigma_a >= 0, sigma_s >= 0 and source q (added to the u_0 equation), each

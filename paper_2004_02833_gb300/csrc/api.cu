@@ -296,7 +296,7 @@ int choose_kernel(rtpn_ctx* ctx) {
     if (k == RTPN_KERNEL_AUTO) {
         const bool tile_set = ctx->tx || ctx->ty || ctx->tz;
         if (kStageInAuto && stage_supported(ctx->N, ctx->prec, ctx->g.nx) &&
-            (!tile_set || stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->chunks)))
+            (!tile_set || stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->depth)))
             k = RTPN_KERNEL_STAGE;
         else
             k = window_supported(ctx->N, ctx->prec) ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
@@ -305,9 +305,9 @@ int choose_kernel(rtpn_ctx* ctx) {
         if (!stage_supported(ctx->N, ctx->prec, ctx->g.nx))
             return fail(ctx, RTPN_EUNSUPPORTED,
                         "staged kernel not compiled for this N/precision or nx*elem not 16-byte rows");
-        if (!stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->chunks))
-            return fail(ctx, RTPN_EUNSUPPORTED, "no staged kernel compiled for this tile / chunk count");
-        int rc = stage_prepare(ctx, ctx->tx, ctx->ty, ctx->tz, ctx->chunks);
+        if (!stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->depth))
+            return fail(ctx, RTPN_EUNSUPPORTED, "no staged kernel compiled for this tile / stage depth");
+        int rc = stage_prepare(ctx, ctx->tx, ctx->ty, ctx->tz, ctx->depth);
         if (rc) return fail(ctx, RTPN_ECUDA, std::string("staged kernel set-up: ") +
                                                  cudaGetErrorString((cudaError_t)rc));
     }
@@ -456,9 +456,9 @@ int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_
     return rtpn_set_kernel_ex(ctx, kernel, tile_x, tile_y, tile_z, 0);
 }
 
-int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z, int chunks) {
+int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z, int depth) {
     if (!ctx) return RTPN_EINVAL;
-    if (chunks < 0 || chunks > 64) return fail(ctx, RTPN_EINVAL, "bad chunk count");
+    if (depth < 0 || depth > 8) return fail(ctx, RTPN_EINVAL, "bad stage depth");
     if (kernel < RTPN_KERNEL_AUTO || kernel > RTPN_KERNEL_STAGE)
         return fail(ctx, RTPN_EINVAL, "unknown kernel");
     if (tile_x < 0 || tile_y < 0 || tile_z < 0) return fail(ctx, RTPN_EINVAL, "bad tile");
@@ -468,13 +468,13 @@ int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int ti
         if (th > 256 || th % 32 != 0)
             return fail(ctx, RTPN_EINVAL, "tile must hold a multiple of 32 threads, at most 256");
     }
-    const int old = ctx->kernel, ox = ctx->tx, oy = ctx->ty, oz = ctx->tz, oc = ctx->chunks;
+    const int old = ctx->kernel, ox = ctx->tx, oy = ctx->ty, oz = ctx->tz, oc = ctx->depth;
     ctx->kernel = kernel;
     drop_graphs(ctx);
     ctx->tx = tile_x;
     ctx->ty = tile_y;
     ctx->tz = tile_z;
-    ctx->chunks = kernel == RTPN_KERNEL_STAGE || kernel == RTPN_KERNEL_AUTO ? chunks : 0;
+    ctx->depth = kernel == RTPN_KERNEL_STAGE || kernel == RTPN_KERNEL_AUTO ? depth : 0;
     int rc = choose_kernel(ctx);
     if (rc) {
         const std::string msg = ctx->err;
@@ -482,7 +482,7 @@ int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int ti
         ctx->tx = ox;
         ctx->ty = oy;
         ctx->tz = oz;
-        ctx->chunks = oc;
+        ctx->depth = oc;
         choose_kernel(ctx);
         ctx->err = msg;
     }
@@ -685,7 +685,7 @@ int rtpn_get_info(const rtpn_ctx* ctx, rtpn_info* out) {
     out->tile[0] = ctx->tx;
     out->tile[1] = ctx->ty;
     out->tile[2] = ctx->tz;
-    out->chunks = ctx->active_kernel == RTPN_KERNEL_STAGE ? ctx->chunks : 1;
+    out->depth = ctx->active_kernel == RTPN_KERNEL_STAGE ? ctx->depth : 1;
     return RTPN_OK;
 }
 

@@ -20,7 +20,7 @@ namespace {
 
 struct Tile {
     int x, y, z;
-    int c = 0;  // threads per cell (staged kernel), 0 = not applicable
+    int c = 0;  // stage buffers (staged kernel), 0 = not applicable
 };
 
 const Tile kCandidates[] = {{32, 1, 1},  {32, 2, 1}, {32, 4, 1}, {32, 8, 1}, {32, 1, 2}, {32, 2, 2},
@@ -116,7 +116,7 @@ int rtpn_autotune(rtpn_ctx* ctx, int reps, int tile[3], double* ms_per_step) {
     k << "single kernel=" << kernel << " N=" << ctx->N << " prec=" << ctx->prec << " bc=" << ctx->g.bc << " grid="
       << ctx->g.nx << "x" << ctx->g.ny << "x" << ctx->g.nz << " dev=" << device_key();
     const std::string key = k.str();
-    Tile best{ctx->tx, ctx->ty, ctx->tz, ctx->chunks};
+    Tile best{ctx->tx, ctx->ty, ctx->tz, ctx->depth};
     double best_ms = -1.0;
     {
         std::lock_guard<std::mutex> lock(g_mu);
@@ -144,7 +144,7 @@ int rtpn_autotune(rtpn_ctx* ctx, int reps, int tile[3], double* ms_per_step) {
             return RTPN_ENOMEM;
         }
         cudaMemcpyAsync(snap, ctx->u, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
-        const int otx = ctx->tx, oty = ctx->ty, otz = ctx->tz, oc = ctx->chunks;
+        const int otx = ctx->tx, oty = ctx->ty, otz = ctx->tz, oc = ctx->depth;
         int rc = sweep(
             ctx->stream, reps, cands,
             [&](Tile t) { return rtpn_set_kernel_ex(ctx, kernel, t.x, t.y, t.z, t.c); },

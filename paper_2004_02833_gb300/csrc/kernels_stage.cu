@@ -1,6 +1,7 @@
 // Host side of the TMA-staged kernels: variant registry, tensor maps, coupling tables, launch.
 #include <cudaTypedefs.h>
 
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -10,27 +11,27 @@
 namespace rtpn {
 namespace stg {
 
-#define RTPN_SDECL(n, x, y, z, p)                                                                  \
-    int stage_launch_##n##_##x##_##y##_##z##_##p(int, int, const Args&, int, cudaStream_t);          \
-    int stage_smem_##n##_##x##_##y##_##z##_##p(int, int);
+#define RTPN_SDECL(n, x, y, z, b)                                                                  \
+    int stage_launch_##n##_##x##_##y##_##z##_##b(int, int, const Args&, int, cudaStream_t);          \
+    int stage_smem_##n##_##x##_##y##_##z##_##b(int, int);
 RTPN_STAGE_VARIANTS(RTPN_SDECL)
 #undef RTPN_SDECL
 
 struct Variant {
-    int N, tx, ty, tz, split;
+    int N, tx, ty, tz, depth;
     int (*launch)(int, int, const Args&, int, cudaStream_t);
     int (*smem)(int, int);
 };
-#define RTPN_SENTRY(n, x, y, z, p)                                                      \
-    Variant{n, x, y, z, p, stage_launch_##n##_##x##_##y##_##z##_##p, stage_smem_##n##_##x##_##y##_##z##_##p},
+#define RTPN_SENTRY(n, x, y, z, b)                                                      \
+    Variant{n, x, y, z, b, stage_launch_##n##_##x##_##y##_##z##_##b, stage_smem_##n##_##x##_##y##_##z##_##b},
 static const Variant kVariants[] = {RTPN_STAGE_VARIANTS(RTPN_SENTRY)};
 #undef RTPN_SENTRY
 
-// first compiled variant of order N with this tile (0 = any) and split (0 = any)
-static const Variant* find(int N, int tx, int ty, int tz, int split = 0) {
+// first compiled variant of order N with this tile (0 = any) and depth (0 = any)
+static const Variant* find(int N, int tx, int ty, int tz, int depth = 0) {
     for (const auto& v : kVariants)
         if (v.N == N && (tx == 0 || (v.tx == tx && v.ty == ty && v.tz == tz)) &&
-            (split == 0 || v.split == split))
+            (depth == 0 || v.depth == depth))
             return &v;
     return nullptr;
 }
@@ -72,52 +73,46 @@ bool stage_supported(int N, int precision, int nx) {
     return nx % hx == 0;
 }
 
-bool stage_has_tile(int N, int tx, int ty, int tz, int split) {
-    return stg::find(N, tx, ty, tz, split) != nullptr;
+bool stage_has_tile(int N, int tx, int ty, int tz, int depth) {
+    return stg::find(N, tx, ty, tz, depth) != nullptr;
 }
 
-int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int split) {
-    const stg::Variant* v = stg::find(ctx->N, tx, ty, tz, split);
+int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
+    const stg::Variant* v = stg::find(ctx->N, tx, ty, tz, depth);
     if (!v) return (int)cudaErrorNotSupported;
     // default (no tile given): the first listed variant whose width divides nx, else the first one
     if (tx == 0)
         for (const auto& w : stg::kVariants)
-            if (w.N == ctx->N && (split == 0 || w.split == split) && ctx->g.nx % w.tx == 0) {
+            if (w.N == ctx->N && (depth == 0 || w.depth == depth) && ctx->g.nx % w.tx == 0) {
                 v = &w;
                 break;
             }
+    const int N = ctx->N;
     const int es = ctx->prec == RTPN_BF16 ? 2 : 4;
     const int hx = 16 / es;
     // the four tensor maps live in device global memory (64-byte aligned) and the kernel reads
-    // them from there: tile box, x-halo group, y-halo row, z-halo plane, each spanning the N/2 + 1
-    // consecutive components of a (type, |m|) run
-    const int nl = ctx->N / 2 + 1;
+    // them from there: tile box, x-halo group, y-halo row, z-halo plane, each spanning E consecutive
+    // components of a (type, |m|) run
+    const int e = stg::box_comps(N, v->tx, v->ty, v->tz, es);
+    if (e <= 0) return (int)cudaErrorInvalidValue;
     alignas(64) CUtensorMap maps[4];
-    if (!stg::make_map(&maps[0], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, v->tz, nl) ||
-        !stg::make_map(&maps[1], ctx->u, ctx->prec, ctx->g, ctx->md.nc, hx, v->ty, v->tz, nl) ||
-        !stg::make_map(&maps[2], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, 1, v->tz, nl) ||
-        !stg::make_map(&maps[3], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, 1, nl))
+    if (!stg::make_map(&maps[0], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, v->tz, e) ||
+        !stg::make_map(&maps[1], ctx->u, ctx->prec, ctx->g, ctx->md.nc, hx, v->ty, v->tz, e) ||
+        !stg::make_map(&maps[2], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, 1, v->tz, e) ||
+        !stg::make_map(&maps[3], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, 1, e))
         return (int)cudaErrorInvalidValue;
     if (!ctx->stage_maps_dev) {
-        cudaError_t e = cudaMalloc(&ctx->stage_maps_dev, sizeof(maps));
-        if (e != cudaSuccess) return (int)e;
+        cudaError_t err = cudaMalloc(&ctx->stage_maps_dev, sizeof(maps));
+        if (err != cudaSuccess) return (int)err;
     }
     {
-        cudaError_t e = cudaMemcpy(ctx->stage_maps_dev, maps, sizeof(maps), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return (int)e;
+        cudaError_t err = cudaMemcpy(ctx->stage_maps_dev, maps, sizeof(maps), cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) return (int)err;
     }
     if (!ctx->stage_mem) {
-        // coupling tables of both classes (CPAD floats per source) and the column starts
-        const int N = ctx->N;
-        std::vector<float> tab[2];
-        for (int A = 0; A < 2; ++A) {
-            std::vector<float> t10;
-            if (!win::coef_table(ctx->md, A, &t10)) return (int)cudaErrorInvalidValue;
-            const size_t ns = t10.size() / 10;
-            tab[A].assign(ns * stg::CPAD, 0.f);
-            for (size_t j = 0; j < ns; ++j)
-                for (int k = 0; k < 10; ++k) tab[A][j * stg::CPAD + k] = t10[j * 10 + k];
-        }
+        // per target class A: the coupling constants of the source class by column, type and run
+        // slot ([N+1][2][N/2+1][CPAD], see stage_impl.cuh), then the column starts of both classes
+        const int nl = N / 2 + 1;
         std::vector<int> col(2 * (N + 2));
         for (int P = 0; P < 2; ++P) {
             int acc = 0;
@@ -126,14 +121,30 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int split) {
                 if (M <= N) acc += win::ntypes(M) * win::column_len(N, M, P);
             }
         }
+        std::vector<float> tab[2];
+        for (int A = 0; A < 2; ++A) {
+            const int B = 1 - A;
+            std::vector<float> t10;  // [local source index of class B][10]
+            if (!win::coef_table(ctx->md, A, &t10)) return (int)cudaErrorInvalidValue;
+            tab[A].assign((size_t)(N + 1) * 2 * nl * stg::CPAD, 0.f);
+            for (int M = 0; M <= N; ++M)
+                for (int t = 0; t < win::ntypes(M); ++t)
+                    for (int j = 0; j < win::column_len(N, M, B); ++j) {
+                        const int src = col[B * (N + 2) + M] + t * win::column_len(N, M, B) + j;
+                        float* d = &tab[A][(((size_t)M * 2 + t) * nl + j) * stg::CPAD];
+                        const float* k = &t10[(size_t)src * 10];
+                        for (int r = 0; r < 6; ++r) d[r] = k[r];      // z, x to M-1, x to M+1
+                        for (int r = 0; r < 4; ++r) d[8 + r] = k[6 + r];  // y to M-1, y to M+1
+                    }
+        }
         const size_t b0 = tab[0].size() * 4, b1 = tab[1].size() * 4, b2 = col.size() * 4;
-        cudaError_t e = cudaMalloc(&ctx->stage_mem, b0 + b1 + b2);
-        if (e != cudaSuccess) return (int)e;
+        cudaError_t err = cudaMalloc(&ctx->stage_mem, b0 + b1 + b2);
+        if (err != cudaSuccess) return (int)err;
         char* m = (char*)ctx->stage_mem;
         cudaMemcpy(m, tab[0].data(), b0, cudaMemcpyHostToDevice);
         cudaMemcpy(m + b0, tab[1].data(), b1, cudaMemcpyHostToDevice);
-        e = cudaMemcpy(m + b0 + b1, col.data(), b2, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return (int)e;
+        err = cudaMemcpy(m + b0 + b1, col.data(), b2, cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) return (int)err;
         ctx->stage_tab_bytes[0] = b0;
         ctx->stage_tab_bytes[1] = b1;
     }
@@ -144,11 +155,11 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int split) {
     ctx->tx = v->tx;
     ctx->ty = v->ty;
     ctx->tz = v->tz;
-    ctx->chunks = v->split;
+    ctx->depth = v->depth;
     return 0;
 }
 
-// the compiled (tile, split) choices of order N, for the tuner
+// the compiled (tile, depth) choices of order N, for the tuner
 int stage_variants_of(int N, int* tiles, int max) {
     int n = 0;
     for (const auto& v : stg::kVariants)
@@ -156,7 +167,7 @@ int stage_variants_of(int N, int* tiles, int max) {
             tiles[4 * n] = v.tx;
             tiles[4 * n + 1] = v.ty;
             tiles[4 * n + 2] = v.tz;
-            tiles[4 * n + 3] = v.split;
+            tiles[4 * n + 3] = v.depth;
             ++n;
         }
     return n;
@@ -171,7 +182,7 @@ int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long
     a.fac = (const float*)ctx->fac;
     // class cls's targets read the coefficients of the other class's sources (table A = cls)
     const char* m = (const char*)ctx->stage_mem;
-    a.coef = (const float*)(cls == 0 ? m : m + ctx->stage_tab_bytes[0]);
+    a.coefcol = (const float*)(cls == 0 ? m : m + ctx->stage_tab_bytes[0]);
     a.colstart = (const int*)(m + ctx->stage_tab_bytes[0] + ctx->stage_tab_bytes[1]);
     a.V = ctx->g.V;
     a.nx = ctx->g.nx;
@@ -184,8 +195,14 @@ int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long
     a.nty = (a.ny + v.ty - 1) / v.ty;
     a.ntz = (a.nz + v.tz - 1) / v.tz;
     a.tiles = (long long)a.ntx * a.nty * a.ntz;
-    // the kernel counts tiles and per-CTA stages in 32 bits
     if (a.tiles * (ctx->N + 2) >= (1ll << 31)) return (int)cudaErrorInvalidValue;
+    // z chunk of the tile walk: the ~one tile per SM at work at a time then spans about as many
+    // tile rows in y as layers in z, across the whole x extent
+    {
+        const double side = std::sqrt((double)(ctx->sms > 0 ? ctx->sms : 1) / a.ntx);
+        int kz = (int)(side + 0.5);
+        a.kz = kz < 1 ? 1 : (kz > a.ntz ? a.ntz : kz);
+    }
     a.maps = (const CUtensorMap*)ctx->stage_maps_dev;
     a.nc = ctx->md.nc;
     a.status = ctx->status;

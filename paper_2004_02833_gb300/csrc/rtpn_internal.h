@@ -86,11 +86,11 @@ HostTable transposed_table(const Model& md, int clsB, double h);
 // ---- TMA-staged kernels (kernels_stage.cu, stage.cu) ----
 // nx must give 16-byte rows for the tensor maps
 bool stage_supported(int N, int precision, int nx);
-bool stage_has_tile(int N, int tx, int ty, int tz, int split);
-// builds the tensor maps (tile 0,0,0 = default; split 0 = any) and the coupling tables;
+bool stage_has_tile(int N, int tx, int ty, int tz, int depth);
+// builds the tensor maps (tile 0,0,0 = default; depth 0 = any) and the coupling tables;
 // returns cudaError_t
-int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int split);
-// compiled (tx, ty, tz, split) of order N into tiles[4*i..]; returns the count
+int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth);
+// compiled (tx, ty, tz, depth) of order N into tiles[4*i..]; returns the count
 int stage_variants_of(int N, int* tiles, int max);
 int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long skip_stage,
                  long long wait_limit);
@@ -103,7 +103,7 @@ struct rtpn_ctx {
     rtpn::Geom g{};
     int N = 0, prec = RTPN_FP32, kernel = RTPN_KERNEL_AUTO, active_kernel = RTPN_KERNEL_GENERIC;
     int tx = 0, ty = 0, tz = 0;
-    int chunks = 0;                  // threads per cell (component chunks) of the staged kernel, 0 = any
+    int depth = 0;                   // stage buffers of the staged kernel, 0 = any
     double dt = 0;
     size_t elem = 4;                 // bytes per stored moment
     void* u = nullptr;               // state [internal c][z][y][x]

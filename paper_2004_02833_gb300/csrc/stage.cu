@@ -1,14 +1,15 @@
 // One variant of the TMA-staged substep kernel: order RTPN_SN, CTA tile RTPN_STX x RTPN_STY x
-// RTPN_STZ, both target classes, FP32 and BF16 storage.  kernels_stage.cu dispatches to it.
+// RTPN_STZ, RTPN_SNB stage buffers, both target classes, FP32 and BF16 storage.  kernels_stage.cu
+// dispatches to it.
 #include "stage_impl.cuh"
 
-#if !defined(RTPN_SN) || !defined(RTPN_STX) || !defined(RTPN_STY) || !defined(RTPN_STZ) || !defined(RTPN_SSPLIT)
-#error "compile with -DRTPN_SN=<order> -DRTPN_STX=.. -DRTPN_STY=.. -DRTPN_STZ=.. -DRTPN_SSPLIT=.."
+#if !defined(RTPN_SN) || !defined(RTPN_STX) || !defined(RTPN_STY) || !defined(RTPN_STZ) || !defined(RTPN_SNB)
+#error "compile with -DRTPN_SN=<order> -DRTPN_STX=.. -DRTPN_STY=.. -DRTPN_STZ=.. -DRTPN_SNB=.."
 #endif
 
 #define RTPN_SCAT2(a, b, c, d, e, f) a##_##b##_##c##_##d##_##e##_##f
 #define RTPN_SCAT(a, b, c, d, e, f) RTPN_SCAT2(a, b, c, d, e, f)
-#define RTPN_SVARIANT(name) RTPN_SCAT(name, RTPN_SN, RTPN_STX, RTPN_STY, RTPN_STZ, RTPN_SSPLIT)
+#define RTPN_SVARIANT(name) RTPN_SCAT(name, RTPN_SN, RTPN_STX, RTPN_STY, RTPN_STZ, RTPN_SNB)
 
 namespace rtpn {
 namespace stg {
@@ -17,18 +18,18 @@ namespace stg {
 // defines a k_stage / launch_one of the same name, and the linker must not merge them.
 namespace {
 
-constexpr int kN = RTPN_SN, kTX = RTPN_STX, kTY = RTPN_STY, kTZ = RTPN_STZ, kSplit = RTPN_SSPLIT;
-constexpr int kThreads = kTX * kTY * kTZ * kSplit;
+constexpr int kN = RTPN_SN, kTX = RTPN_STX, kTY = RTPN_STY, kTZ = RTPN_STZ, kNB = RTPN_SNB;
+constexpr int kThreads = Layout<kN, 0, float, kTX, kTY, kTZ, kNB>::THREADS;
 
 template <int A, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_stage(Args a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    stage_kernel_body<kN, A, S, kTX, kTY, kTZ, kSplit>(a, smem);
+    stage_kernel_body<kN, A, S, kTX, kTY, kTZ, kNB>(a, smem);
 }
 
 template <int A, typename S>
 int launch_one(const Args& a, int sms, cudaStream_t st) {
-    using L = Layout<kN, A, S, kTX, kTY, kTZ>;
+    using L = Layout<kN, A, S, kTX, kTY, kTZ, kNB>;
     static bool configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -58,11 +59,12 @@ int RTPN_SVARIANT(stage_launch)(int cls, int precision, const Args& a, int sms, 
     return cls == 0 ? launch_one<0, float>(a, sms, st) : launch_one<1, float>(a, sms, st);
 }
 
+// dynamic shared memory of the variant, or 0 if it does not fit a CTA
 int RTPN_SVARIANT(stage_smem)(int cls, int precision) {
     if (precision == RTPN_BF16)
-        return cls == 0 ? Layout<kN, 0, __nv_bfloat16, kTX, kTY, kTZ>::BYTES
-                        : Layout<kN, 1, __nv_bfloat16, kTX, kTY, kTZ>::BYTES;
-    return cls == 0 ? Layout<kN, 0, float, kTX, kTY, kTZ>::BYTES : Layout<kN, 1, float, kTX, kTY, kTZ>::BYTES;
+        return cls == 0 ? Layout<kN, 0, __nv_bfloat16, kTX, kTY, kTZ, kNB>::BYTES
+                        : Layout<kN, 1, __nv_bfloat16, kTX, kTY, kTZ, kNB>::BYTES;
+    return cls == 0 ? Layout<kN, 0, float, kTX, kTY, kTZ, kNB>::BYTES : Layout<kN, 1, float, kTX, kTY, kTZ, kNB>::BYTES;
 }
 
 }  // namespace stg

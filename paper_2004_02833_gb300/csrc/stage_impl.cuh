@@ -1,26 +1,33 @@
 // TMA-staged substep kernel with a compact column loop (FP32 arithmetic, FP32 or BF16 storage).
 //
-// Arithmetic as in the register-window kernel (window_impl.cuh): one thread per cell of a CTA tile
-// sweeps the frozen class column by column in |m| and scatters three half-grid differences per
-// source into the accumulators of its <= 10 targets (Eqs. 4-5; Section 3.2's unrolled sparse
-// product), a target column being finished once the next source column is in.  Two things differ:
+// Arithmetic as in the register-window kernel (window_impl.cuh): the frozen class is swept column by
+// column in |m|; every source value yields three half-grid differences (Section 2.1) that are
+// scattered into the accumulators of its <= 10 targets (Eqs. 4-5; Section 3.2's unrolled sparse
+// product), and a target column is finished, by Eq. (5), once the next source column is in.  What
+// differs:
 //
-//  * The column sweep is a runtime loop whose body handles one column for every (type, l) slot of
-//    the class; the three live target columns are three register arrays that shift by one column
-//    per iteration.  Slots that do not exist in a column are skipped (sources) or carry zero
-//    coefficients (targets), so the body is the same for every column and stays small enough for
-//    the instruction cache (the fully unrolled body of the register-window kernel is not).
-//  * The data of a column reach shared memory through the Tensor Memory Accelerator
-//    (cp.async.bulk.tensor), double buffered: while column M is computed the copies of column M+1
-//    are in flight.  A column stage holds, per source component, the tile box plus one halo slab on
-//    the side its partners read along each axis (x: an aligned 16-byte group, y: one row, z: one
-//    plane), and, per target component of the column being finished, its tile box.  Periodic halos
-//    use wrapped coordinates; vacuum halos use out-of-range coordinates, which the TMA unit fills
-//    with zeros.  The coupling constants sit in shared memory.
+//  * Two threads share a cell, one per target type (cos / sin).  Targets of type T take their z and
+//    x differences from sources of type T and their y differences from sources of the other type
+//    (Eq. 3's Mx and Mz keep the type, My swaps it), so the split needs no exchange and the two
+//    threads carry equal work.  Each thread keeps three columns of N/2 + 1 accumulators.
+//  * The column sweep is a runtime loop whose body handles one column for every l slot; the three
+//    live target columns are register arrays that shift by one column per iteration, so the body
+//    is the same for every column and fits the instruction cache.
+//  * A producer warp moves each source column into shared memory with the Tensor Memory
+//    Accelerator (cp.async.bulk.tensor): per type and box kind, boxes of E consecutive components
+//    of the (type, |m|) run, as many as the column needs.  A column stage holds, per source
+//    component, the tile box plus one halo slab on the side its partners read along each axis (x:
+//    an aligned 16-byte group, y: one row, z: one plane), and the column's coupling constants (a
+//    plain bulk copy).  Periodic halos use wrapped coordinates; vacuum halos use out-of-range
+//    coordinates, which the TMA unit fills with zeros.  The same stage carries the tile boxes of
+//    the target column it finishes (column i - 1 in stage i; a tile has N + 2 stages).  NB stage
+//    buffers form a ring with a full / empty mbarrier pair each, so up to NB - 1 stages are in
+//    flight while one is computed.
 //
-// CTAs are persistent (one per SM) and walk tiles in z-fastest order; the stage sequence runs on
-// across tiles so the pipeline never drains.  Every mbarrier wait is bounded: one that runs out
-// sets a status bit, and the CTA leaves after a second bounded wait for the copies in flight.
+// CTAs are persistent (one per SM) and walk tiles in z-chunked order (z fastest inside a chunk of kz
+// tile layers, then x, then y), so the CTAs at work at any time cover a compact block and read one
+// another's halos from L2.  Every mbarrier wait is bounded: one that runs out sets a status bit,
+// the warp leaves, and the producer waits (bounded) for the copies it issued before the CTA ends.
 #pragma once
 
 #include <cuda.h>
@@ -36,58 +43,116 @@ using win::first_l;
 using win::ntypes;
 using win::static_for;
 
+// Enter a compile-time unrolled slot sequence at a runtime slot: `switch (first) {
+// RTPN_SLOT_CASES(f) }` runs f(q) for q = first, first + 1, ... 23 (f ignores q past its range), one
+// jump per column instead of a test per slot.
+#define RTPN_SLOT_CASE(f, q)                   \
+    case q:                                    \
+        f(std::integral_constant<int, q>{});   \
+        [[fallthrough]];
+#define RTPN_SLOT_CASES(f)                                                                          \
+    RTPN_SLOT_CASE(f, 0) RTPN_SLOT_CASE(f, 1) RTPN_SLOT_CASE(f, 2) RTPN_SLOT_CASE(f, 3)             \
+    RTPN_SLOT_CASE(f, 4) RTPN_SLOT_CASE(f, 5) RTPN_SLOT_CASE(f, 6) RTPN_SLOT_CASE(f, 7)             \
+    RTPN_SLOT_CASE(f, 8) RTPN_SLOT_CASE(f, 9) RTPN_SLOT_CASE(f, 10) RTPN_SLOT_CASE(f, 11)           \
+    RTPN_SLOT_CASE(f, 12) RTPN_SLOT_CASE(f, 13) RTPN_SLOT_CASE(f, 14) RTPN_SLOT_CASE(f, 15)         \
+    RTPN_SLOT_CASE(f, 16) RTPN_SLOT_CASE(f, 17) RTPN_SLOT_CASE(f, 18) RTPN_SLOT_CASE(f, 19)         \
+    RTPN_SLOT_CASE(f, 20) RTPN_SLOT_CASE(f, 21) RTPN_SLOT_CASE(f, 22) RTPN_SLOT_CASE(f, 23)         \
+    default:                                                                                        \
+        break;
+constexpr int kMaxSlots = 24;
+
 constexpr unsigned STATUS_TIMEOUT = 1u;
 constexpr unsigned STATUS_CHECK = 2u;  // a self-check failed (builds with RTPN_STAGE_CHECKS)
-constexpr int CPAD = 12;  // coefficients per source in shared memory (10 used), three float4
+// coupling constants per source slot, three float4:
+//   [0..3] z (l-1), z (l+1), x to column M-1 (l-1), (l+1)     read by the thread of the same type
+//   [4..5] x to column M+1 (l-1), (l+1); [6..7] unused        read by the thread of the same type
+//   [8..11] y to column M-1 (l-1), (l+1), to M+1 (l-1), (l+1)  read by the thread of the other type
+constexpr int CPAD = 12;
 
 struct Args {
     void* u;
     const float* fac;
-    const float* coef;      // [class-B source][CPAD] in global memory (copied to shared memory)
+    const float* coefcol;   // [column 0..N][type][run slot 0..N/2][CPAD] of the source class
     const int* colstart;    // [2][N+2]: first local index of column M in class 0 / class 1
     long long V;
     int nx, ny, nz, bc;
     int fac_ofs;
     float inv_h;
     int ntx, nty, ntz;
+    int kz;                 // tile layers per z chunk of the walk
     long long tiles;
     const CUtensorMap* maps;  // four tensor maps in global memory: tile, x halo, y halo, z halo
     int nc;                   // components (bound of the 4th tensor coordinate)
     unsigned* status;       // device status word (STATUS_TIMEOUT on a wait that ran out)
     long long wait_limit;   // try_wait polls before giving up
-    long long skip_stage;   // global stage index never issued (a wait that must run out); -1 normally
+    long long skip_stage;   // stage index never issued (a wait that must run out); -1 normally
 };
 
 __host__ __device__ constexpr int pad128(int bytes) { return (bytes + 127) / 128 * 128; }
 
-template <int N, int A, typename S, int TX, int TY, int TZ>
+// Components per TMA box along the component axis.  A box lands at a 128-byte aligned shared-memory
+// address, so E times the bytes of one component of every box kind (tile, x halo, y halo, z halo)
+// must be a multiple of 128; among such E <= 8 the one that holds a run of N/2 + 1 in the fewest
+// slots, then in the fewest boxes, is taken.
+__host__ __device__ constexpr int box_comps(int N, int tx, int ty, int tz, int es) {
+    const int nl0 = N / 2 + 1;
+    const int kinds[4] = {tx * ty * tz * es, (16 / es) * ty * tz * es, tx * tz * es, tx * ty * es};
+    int best = 0, best_slots = 1 << 30;
+    for (int e = 8; e >= 1; --e) {
+        bool ok = true;
+        for (int k = 0; k < 4; ++k) ok = ok && (e * kinds[k]) % 128 == 0;
+        const int slots = (nl0 + e - 1) / e * e;
+        if (ok && slots < best_slots) {
+            best = e;
+            best_slots = slots;
+        }
+    }
+    return best;  // 0: no aligned box exists for this tile
+}
+__host__ __device__ constexpr int run_slots(int N, int e) { return e > 0 ? (N / 2 + e) / e * e : 0; }
+
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB>
 struct Layout {
     static constexpr int B = 1 - A;
-    static constexpr int NL = N / 2 + 1;  // components per (type, |m|) run, at most
     static constexpr int ES = (int)sizeof(S);
+    static constexpr int E = box_comps(N, TX, TY, TZ, ES);  // components per box
+    static constexpr int NL = run_slots(N, E);              // run slots per type in shared memory
+    static constexpr int NG = NL / E;                       // boxes per run, at most
+    static constexpr int NLC = N / 2 + 1;                   // coupling-constant slots per type
     static constexpr int HX = 16 / ES;    // x halo: one aligned 16-byte group
+    static constexpr int CELLS = TX * TY * TZ;
+    static constexpr int CONSUMER_WARPS = 2 * CELLS / 32;
+    static constexpr int THREADS = 2 * CELLS + 32;          // two threads per cell + the producer
     // bytes of one component in each box kind
     static constexpr int CTR_BYTES = TX * TY * TZ * ES;
     static constexpr int HX_BYTES = HX * TY * TZ * ES;
     static constexpr int HY_BYTES = TX * TZ * ES;
     static constexpr int HZ_BYTES = TX * TY * ES;
-    // one TMA box carries NL consecutive components of a run; regions per type t:
+    static constexpr int COMP_BYTES = CTR_BYTES + HX_BYTES + HY_BYTES + HZ_BYTES;
+    // regions of one type: the run's tile boxes, then its x, y and z halos
     static constexpr int R_CTR = pad128(NL * CTR_BYTES);
     static constexpr int R_HX = pad128(NL * HX_BYTES);
     static constexpr int R_HY = pad128(NL * HY_BYTES);
     static constexpr int R_HZ = pad128(NL * HZ_BYTES);
-    static constexpr int SRC_T = R_CTR + R_HX + R_HY + R_HZ;   // source regions of one type
+    static constexpr int SRC_T = R_CTR + R_HX + R_HY + R_HZ;
     static constexpr int HXO = R_CTR, HYO = R_CTR + R_HX, HZO = R_CTR + R_HX + R_HY;
-    static constexpr int TGT0 = 2 * SRC_T;                       // target regions after the sources
-    static constexpr int BUF = TGT0 + 2 * R_CTR;
-    static constexpr int SRC_TX = NL * (CTR_BYTES + HX_BYTES + HY_BYTES + HZ_BYTES);  // per run
-    static constexpr int TGT_TX = NL * CTR_BYTES;
-    static constexpr int COEF = pad128(class_size(N, B) * CPAD * 4);
-    static constexpr int BYTES = COEF + 2 * BUF + 128 + 128;  // table, two buffers, mbarriers,
-                                                              // and slack to align the base to 128 B
+    static constexpr int COEF_COL = 2 * NLC * CPAD * 4;     // one column's coupling constants
+    static constexpr int R_TGT = pad128(NL * CTR_BYTES);     // tile boxes of one type's targets
+    static constexpr int TGTO = 2 * SRC_T;
+    static constexpr int COEFO = TGTO + 2 * R_TGT;
+    static constexpr int BUF = COEFO + pad128(COEF_COL);     // one stage buffer
+    static constexpr int BARS = pad128(2 * NB * 8);
+    static constexpr int BYTES = NB * BUF + BARS + 128;      // ring, mbarriers, base alignment slack
     static_assert(TX % HX == 0, "tile width must be a multiple of the 16-byte group");
+    static_assert(CELLS % 32 == 0, "a type's threads must fill whole warps");
     static_assert(CTR_BYTES % 16 == 0 && HX_BYTES % 16 == 0 && HY_BYTES % 16 == 0 && HZ_BYTES % 16 == 0,
                   "box components must stay 16-byte aligned");
+    static_assert(NB >= 2 && NB <= 8, "two to eight stage buffers");
+    static_assert(E > 0, "no 128-byte aligned box for this tile");
+    static_assert((E * CTR_BYTES) % 128 == 0 && (E * HX_BYTES) % 128 == 0 && (E * HY_BYTES) % 128 == 0 &&
+                      (E * HZ_BYTES) % 128 == 0 && BUF % 128 == 0,
+                  "every box must land on a 128-byte boundary");
+    static_assert(BYTES <= 232448, "stage ring exceeds the 227 KB of shared memory of a CTA");
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -100,6 +165,9 @@ __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     unsigned ok;
@@ -120,6 +188,12 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map
         "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(c), "r"(bar)
         : "memory");
 }
+__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(bar)
+        : "memory");
+}
 // bounded wait on one mbarrier phase; false if it ran out
 __device__ __forceinline__ bool wait_phase(unsigned bar, unsigned parity, long long limit) {
     for (long long i = 0; i < limit; ++i)
@@ -136,27 +210,21 @@ __device__ __forceinline__ float lds(const unsigned char* base, int byte_off) {
     }
 }
 
-// Optional self-checks (compile with -DRTPN_STAGE_CHECKS): an index or alignment that breaks the
-// layout sets STATUS_CHECK and the access is skipped.
-// With the checks on, status[1..] is a diagnostic record: [1] id of the first failed check,
-// [2] a value of it, [3] issue() calls, [4] successful waits, [5] stage of a timeout + 1,
-// [6] copies issued.
+// Optional self-checks (compile with -DRTPN_STAGE_CHECKS): an index that breaks the layout sets
+// STATUS_CHECK and the access is skipped.  status[1] holds the id of the first failed check,
+// status[2] a value of it, status[7] the block.
 #ifdef RTPN_STAGE_CHECKS
 __device__ __forceinline__ bool scheck_fail(unsigned* st, unsigned id, unsigned val, unsigned aux) {
     atomicOr(st, STATUS_CHECK);
-    if (atomicCAS(st + 1, 0u, id) == 0u) {  // the first failure keeps its details
+    if (atomicCAS(st + 1, 0u, id) == 0u) {
         st[2] = val;
         st[7] = aux;
     }
     return false;
 }
-#define RTPN_SCHECK_AUX(cond, id, val, aux) ((cond) ? true : scheck_fail(a.status, (id), (unsigned)(val), (unsigned)(aux)))
-#define RTPN_SCHECK_ID(cond, id, val) RTPN_SCHECK_AUX(cond, id, val, blockIdx.x)
-#define RTPN_SCOUNT(slot) atomicAdd(a.status + (slot), 1u)
+#define RTPN_SCHECK_ID(cond, id, val) ((cond) ? true : scheck_fail(a.status, (id), (unsigned)(val), blockIdx.x))
 #else
-#define RTPN_SCHECK_AUX(cond, id, val, aux) true
 #define RTPN_SCHECK_ID(cond, id, val) true
-#define RTPN_SCOUNT(slot) ((void)0)
 #endif
 #define RTPN_SCHECK(cond) RTPN_SCHECK_ID(cond, __LINE__, 0)
 
@@ -167,16 +235,35 @@ struct TileGeo {
     int hx_start[2], hx_elem[2];
 };
 
-// Tile t (t < 2^31, checked on the host) of the walk: z fastest, then x, then y.  32-bit division:
-// this runs once per tile and thread.
+// tile t of the walk: chunks of kz z-layers; inside a chunk z fastest, then x, then y
+__host__ __device__ __forceinline__ void tile_coords(unsigned t, int ntx, int nty, int ntz, int kzc, int* bx,
+                                                     int* by, int* bz) {
+    const unsigned per_chunk = (unsigned)kzc * ntx * nty;
+    const unsigned full = (unsigned)(ntz / kzc);
+    unsigned chunk, r, kz;
+    if (t < full * per_chunk) {
+        chunk = t / per_chunk;
+        r = t - chunk * per_chunk;
+        kz = kzc;
+    } else {
+        chunk = full;
+        r = t - full * per_chunk;
+        kz = ntz - full * kzc;
+    }
+    *bz = (int)(chunk * kzc + r % kz);
+    const unsigned rest = r / kz;
+    *bx = (int)(rest % ntx);
+    *by = (int)(rest / ntx);
+}
+
 template <int TX, int TY, int TZ, int HX>
 __device__ __forceinline__ TileGeo tile_geo(const Args& a, unsigned t) {
     TileGeo g;
-    const unsigned bz = t % (unsigned)a.ntz;
-    const unsigned rest = t / (unsigned)a.ntz;
-    g.x0 = (int)(rest % (unsigned)a.ntx) * TX;
-    g.y0 = (int)(rest / (unsigned)a.ntx) * TY;
-    g.z0 = (int)bz * TZ;
+    int bx, by, bz;
+    tile_coords(t, a.ntx, a.nty, a.ntz, a.kz, &bx, &by, &bz);
+    g.x0 = bx * TX;
+    g.y0 = by * TY;
+    g.z0 = bz * TZ;
     g.wx = min(TX, a.nx - g.x0);
     g.wy = min(TY, a.ny - g.y0);
     g.wz = min(TZ, a.nz - g.z0);
@@ -205,325 +292,328 @@ __device__ __forceinline__ TileGeo tile_geo(const Args& a, unsigned t) {
 // Source x slot: 1 (read at i+1 by its partners) iff (M even) == (cos type); z slot: 1 iff l+M even.
 __device__ __forceinline__ int dir_x(int M, int t) { return ((M & 1) == 0) == (t == 0) ? 1 : -1; }
 
-// SPLIT threads share a cell: part p owns the targets with l/2 in [p NLP, (p+1) NLP) and sweeps the
-// sources that reach them (its range and one neighbouring l on each side), so each thread keeps a
-// window of 3 x 2 x NLP accumulators and the CTA runs SPLIT times as many warps on the same tile.
-template <int N, int A, typename S, int TX, int TY, int TZ, int SPLIT>
-__device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* smem) {
-    using L = Layout<N, A, S, TX, TY, TZ>;
+// The producer warp: issues the copies of every stage of this CTA's sequence into the ring.
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB>
+__device__ __forceinline__ void stage_producer(const Args& a, unsigned char* bufs, unsigned full0,
+                                               unsigned empty0, int total) {
+    using L = Layout<N, A, S, TX, TY, TZ, NB>;
     constexpr int B = 1 - A;
-    constexpr int NL = L::NL;
-    constexpr int CELLS = TX * TY * TZ;
-    constexpr int NLP = (NL + SPLIT - 1) / SPLIT;
-    constexpr int HX = L::HX;
-    constexpr int NSTAGE = N + 2;  // stage i: sources of column i (i <= N), targets of column i-1
+    constexpr int NST = N + 2;
+    constexpr int E = L::E, NG = L::NG;
+    const int lane = threadIdx.x & 31;
     const int cA0 = A == 0 ? 0 : class_size(N, 0);
     const int cB0 = B == 0 ? 0 : class_size(N, 0);
     const int* colA = a.colstart + A * (N + 2);
     const int* colB = a.colstart + B * (N + 2);
+    const CUtensorMap* maps = a.maps;
+    // the maps were written by the host before the launch; make them visible to the async proxy
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + k) : "memory");
+
+    int s = 0;
+    bool failed = false;
+    int b = 0, i = 0;
+    unsigned ph = 0;  // phase parity of buffer b's current use (flips when b wraps)
+    unsigned tile = blockIdx.x;
+    TileGeo g = tile_geo<TX, TY, TZ, L::HX>(a, tile);
+    for (; s < total; ++s, i = (i == NST - 1) ? 0 : i + 1) {
+        if (i == 0 && s > 0) {
+            tile += gridDim.x;
+            g = tile_geo<TX, TY, TZ, L::HX>(a, tile);
+        }
+        const unsigned full = full0 + 8 * b;
+        if (s >= NB) {  // the consumers must have released the buffer's previous stage
+            const bool ok = __all_sync(0xffffffffu, wait_phase(empty0 + 8 * b, ph ^ 1u, a.wait_limit));
+            if (!ok) {
+                failed = true;
+                break;
+            }
+        }
+        const int bcur = b;
+        if (++b == NB) {
+            b = 0;
+            ph ^= 1u;
+        }
+        if (s == a.skip_stage) continue;
+        unsigned char* buf = bufs + bcur * L::BUF;
+        const int len = column_len(N, i, B);     // sources of column i (none at i = N + 1)
+        const int nt = len > 0 ? ntypes(i) : 0;  // source types present in the column
+        const int nbox = (len + E - 1) / E;
+        const int M = i - 1;                     // target column finished in this stage
+        const int lenA = M >= 0 ? column_len(N, M, A) : 0;
+        const int ntA = lenA > 0 ? ntypes(M) : 0;
+        const int nboxA = (lenA + E - 1) / E;
+        const unsigned bytes = nt * nbox * E * L::COMP_BYTES + ntA * nboxA * E * L::CTR_BYTES +
+                               (nt > 0 ? L::COEF_COL : 0);
+        if (lane == 0) mbar_expect_tx(full, bytes);
+        __syncwarp();
+        // lane j < 8 NG: source box (type j / (4 NG), kind (j / NG) % 4, box j % NG);
+        // 8 NG <= j < 10 NG: target box (type (j - 8 NG) / NG, box j % NG)
+        for (int j = lane; j < 10 * NG; j += 32) {
+            if (j >= 8 * NG) {
+                const int t = (j - 8 * NG) / NG, k = j % NG;
+                if (t >= ntA || k >= nboxA) continue;
+                const int c = cA0 + colA[M] + t * lenA + k * E;
+                if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 111, c)) continue;
+                tma_load_4d(smem_addr(buf + L::TGTO + t * L::R_TGT) + k * E * L::CTR_BYTES, maps, g.x0, g.y0,
+                            g.z0, c, full);
+                continue;
+            }
+            const int t = j / (4 * NG), kind = (j / NG) % 4, k = j % NG;
+            if (t >= nt || k >= nbox) continue;
+            const int c = cB0 + colB[i] + t * len + k * E;  // first component of the box
+            const unsigned d = smem_addr(buf + t * L::SRC_T);
+            if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 101, c)) continue;
+            if (kind == 0) {
+                tma_load_4d(d + k * E * L::CTR_BYTES, maps, g.x0, g.y0, g.z0, c, full);
+            } else if (kind == 1) {  // x slot 1 -> partners read i+1 (upper halo)
+                const int hxs = dir_x(i, t) > 0 ? g.hx_start[1] : g.hx_start[0];
+                tma_load_4d(d + L::HXO + k * E * L::HX_BYTES, maps + 1, hxs, g.y0, g.z0, c, full);
+            } else if (kind == 2) {  // cos type reads y+1, sin type y-1
+                tma_load_4d(d + L::HYO + k * E * L::HY_BYTES, maps + 2, g.x0, t == 0 ? g.hc[1][1] : g.hc[1][0],
+                            g.z0, c, full);
+            } else {                 // z slot 1 (l + M even) reads z+1
+                tma_load_4d(d + L::HZO + k * E * L::HZ_BYTES, maps + 3, g.x0, g.y0,
+                            ((B + i) & 1) == 0 ? g.hc[2][1] : g.hc[2][0], c, full);
+            }
+        }
+        if (lane == 0 && nt > 0)
+            bulk_load(smem_addr(buf + L::COEFO), a.coefcol + (long long)i * (2 * L::NLC * CPAD), L::COEF_COL,
+                      full);
+    }
+    if (failed && lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
+    // before the CTA ends, the copies of the last stages issued must have landed
+    const int first = s > NB ? s - NB : 0;
+    for (int r = first; r < s; ++r)
+        if (r != a.skip_stage) wait_phase(full0 + 8 * (r % NB), (unsigned)((r / NB) & 1), a.wait_limit);
+}
+
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB>
+__device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* smem) {
+    using L = Layout<N, A, S, TX, TY, TZ, NB>;
+    static_assert(N >= 1, "order N >= 1");
+    static_assert((N + 2) / 2 <= kMaxSlots, "slot switch covers N <= 45");
+    constexpr int B = 1 - A;
+    constexpr int NLA = (N - A) / 2 + 1;   // class-A components of a run, at most
+    constexpr int NLB = (N - B) / 2 + 1;   // class-B components of a run, at most
+    constexpr int CELLS = L::CELLS;
+    constexpr int HX = L::HX;
+    constexpr int NST = N + 2;  // stage i: sources of column i (i <= N), targets of column i - 1
+    const int cA0 = A == 0 ? 0 : class_size(N, 0);
+    const int* colA = a.colstart + A * (N + 2);
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int part = tid / CELLS, ctid = tid % CELLS;
-    const int lx = ctid % TX, ly = (ctid / TX) % TY, lz = ctid / (TX * TY);
+    const int warp = tid >> 5, lane = tid & 31;
     const long long V = a.V;
 
     // TMA writes into shared memory need 128-byte aligned destinations; the dynamic shared memory
     // window is not guaranteed to start on one, so the layout starts at the next 128-byte boundary.
     smem += (128u - (smem_addr(smem) & 127u)) & 127u;
-    float* coef = reinterpret_cast<float*>(smem);
-    unsigned char* bufs = smem + L::COEF;
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(bufs + 2 * L::BUF);
-    const unsigned bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
-
-    const CUtensorMap* map_ctr = a.maps;
-    const CUtensorMap* map_hx = a.maps + 1;
-    const CUtensorMap* map_hy = a.maps + 2;
-    const CUtensorMap* map_hz = a.maps + 3;
-
-    // coupling constants into shared memory
-    for (int i = tid; i < class_size(N, B) * CPAD; i += CELLS * SPLIT) coef[i] = a.coef[i];
-    if (tid < 4) {
-        // the maps were written by the host before the launch; make them visible to the async proxy
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(a.maps + tid)
-                     : "memory");
-    }
-#ifdef RTPN_STAGE_CHECKS
+    unsigned char* bufs = smem;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + NB * L::BUF);
+    const unsigned full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[NB]);
     if (tid == 0) {
-        RTPN_SCHECK_AUX(a.nc == (N + 1) * (N + 1), 121, a.nc, 0);
-        RTPN_SCHECK_AUX(colA[0] == 0 && colA[N + 1] == class_size(N, A), 122, colA[N + 1], colA[1]);
-        RTPN_SCHECK_AUX(colB[0] == 0 && colB[N + 1] == class_size(N, B), 123, colB[N + 1], colB[1]);
-    }
-#endif
-    if (tid == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(full0 + 8 * b, 1);
+            mbar_init(empty0 + 8 * b, L::CONSUMER_WARPS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
 
-    // stages of this CTA (the host keeps tiles * NSTAGE below 2^31)
     const int my_tiles = a.tiles > blockIdx.x ? (int)((a.tiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
-    const int total = my_tiles * NSTAGE;
+    const int total = my_tiles * NST;
+    if (warp == L::CONSUMER_WARPS) {
+        stage_producer<N, A, S, TX, TY, TZ, NB>(a, bufs, full0, empty0, total);
+        return;
+    }
 
-    // Issue stage s of this CTA (column stage i of the tile with geometry g): warp 0.  One TMA box
-    // per (type, box kind) carries the NL consecutive components of a (type, |m|) run starting at
-    // the run's first component: lanes 0-3 the source boxes of type 0, 4-7 of type 1, 8-9 the target
-    // boxes of types 0 and 1.
-    auto issue = [&](int s, int i, const TileGeo& g) {
-        if (s == a.skip_stage) return;
-        unsigned char* buf = bufs + (s & 1) * L::BUF;
-        const unsigned bar = (s & 1) ? bar1 : bar0;
-        const bool src_t[2] = {i <= N && column_len(N, i, B) > 0, i >= 1 && i <= N && column_len(N, i, B) > 0};
-        const int M = i - 1;
-        const bool tgt_t[2] = {M >= 0 && column_len(N, M, A) > 0, M >= 1 && column_len(N, M, A) > 0};
-        const unsigned bytes = (src_t[0] + src_t[1]) * L::SRC_TX + (tgt_t[0] + tgt_t[1]) * L::TGT_TX;
-        if (lane == 0) {
-            mbar_expect_tx(bar, bytes);
-            RTPN_SCOUNT(3);
-        }
-        __syncwarp();
-        if (lane < 8) {
-            const int t = lane / 4, kind = lane % 4;
-            if (!src_t[t]) return;
-            const int c = cB0 + colB[i] + t * column_len(N, i, B);  // first component of the run
-            const unsigned d = smem_addr(buf + t * L::SRC_T);
-            if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 101, c)) return;
-            if (!RTPN_SCHECK_ID((d & 127) == 0, 103, d)) return;
-            RTPN_SCOUNT(6);
-            if (kind == 0) {
-                tma_load_4d(d, map_ctr, g.x0, g.y0, g.z0, c, bar);
-            } else if (kind == 1) {  // x slot 1 -> partners read i+1 (upper halo)
-                const int hxs = dir_x(i, t) > 0 ? g.hx_start[1] : g.hx_start[0];
-                if (!RTPN_SCHECK_ID(hxs % HX == 0, 102, hxs)) return;
-                tma_load_4d(d + L::HXO, map_hx, hxs, g.y0, g.z0, c, bar);
-            } else if (kind == 2) {  // cos type reads y+1, sin type y-1
-                tma_load_4d(d + L::HYO, map_hy, g.x0, t == 0 ? g.hc[1][1] : g.hc[1][0], g.z0, c, bar);
-            } else {                 // z slot 1 (l + M even) reads z+1
-                tma_load_4d(d + L::HZO, map_hz, g.x0, g.y0, ((B + i) & 1) == 0 ? g.hc[2][1] : g.hc[2][0], c,
-                            bar);
-            }
-        } else if (lane < 10) {
-            const int t = lane - 8;
-            if (!tgt_t[t]) return;
-            const int c = cA0 + colA[M] + t * column_len(N, M, A);
-            const unsigned d = smem_addr(buf + L::TGT0 + t * L::R_CTR);
-            if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 111, c)) return;
-            if (!RTPN_SCHECK_ID((d & 127) == 0, 113, d)) return;
-            RTPN_SCOUNT(6);
-            tma_load_4d(d, map_ctr, g.x0, g.y0, g.z0, c, bar);
-        }
-    };
+    // ---- consumers: thread (T, cell) finishes the targets of type T in its cell
+    const int T = tid / CELLS, ctid = tid % CELLS;
+    const int lx = ctid % TX, ly = (ctid / TX) % TY, lz = ctid / (TX * TY);
+    const int my = ((lz * TY + ly) * TX + lx) * L::ES;
 
-    float prev[2][NLP], cur[2][NLP], next[2][NLP];
+    float prev[NLA], cur[NLA], next[NLA];
 #pragma unroll
-    for (int t = 0; t < 2; ++t)
-#pragma unroll
-        for (int q = 0; q < NLP; ++q) prev[t][q] = cur[t][q] = next[t][q] = 0.f;
+    for (int q = 0; q < NLA; ++q) prev[q] = cur[q] = next[q] = 0.f;
 
-    // geometry of the current tile, computed once per tile (and by warp 0 once more for the first
-    // issue into the next tile)
-    unsigned cur_tile = blockIdx.x;
-    TileGeo g = tile_geo<TX, TY, TZ, HX>(a, cur_tile);
-    if (tid < 32 && total > 0) issue(0, 0, g);
-    int fail_at = -1;
-
+    TileGeo g{};
     bool active = false;
     long long cell = 0;
-    float al[8], be[8];
-    float al0 = 0.f, be0 = 0.f, ga0 = 0.f;
-    int my = 0;
-    bool iny[2] = {true, true};
+    float alE = 0.f, beE = 0.f, alO = 0.f, beO = 0.f;  // Eq. (5) factors of columns M even / odd
+    float al0 = 0.f, be0 = 0.f, ga0 = 0.f;             // u_0 (class 0, type 0 only)
 
-    for (int s = 0, i = 0; s < total; ++s, i = (i == NSTAGE - 1) ? 0 : i + 1) {
-        if (i == 0) {  // new tile: geometry, factors, fixed neighbour offsets
-            if (s > 0) {
-                cur_tile += gridDim.x;
-                g = tile_geo<TX, TY, TZ, HX>(a, cur_tile);
-            }
+    // first local index of target column M in class A, advanced column by column (offA = colstart
+    // of the column finished next); component q = 0 of the run (type T, column M) at this cell
+    int offA = 0;
+    auto tgt_ptr = [&](int M) {
+        return reinterpret_cast<S*>(a.u) +
+               (long long)(cA0 + offA + T * column_len(N, M, A) - first_l(M, A) / 2) * V + cell;
+    };
+
+    unsigned tile = blockIdx.x;
+    int b = 0;
+    unsigned ph = 0;
+    for (int s = 0, i = 0; s < total; ++s, i = (i == NST - 1) ? 0 : i + 1) {
+        if (i == 0) {  // new tile: geometry, factors
+            if (s > 0) tile += gridDim.x;
+            g = tile_geo<TX, TY, TZ, HX>(a, tile);
             active = lx < g.wx && ly < g.wy && lz < g.wz;
             cell = ((long long)(g.z0 + lz) * a.ny + (g.y0 + ly)) * a.nx + (g.x0 + lx);
-            my = ((lz * TY + ly) * TX + lx) * L::ES;
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {  // y slot is fixed per type: cos reads y+1, sin y-1
-                const int dy = t == 0 ? 1 : -1;
-                iny[t] = ly + dy >= 0 && ly + dy < g.wy;
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) al[k] = be[k] = 0.f;
             if (active) {
+                // sub-grid slot of (l, M, T) in class A: x by (M, T), y by T, z by (A + M)
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int twos = (k & 1) + ((k >> 1) & 1) + ((k >> 2) & 1);
-                    if (twos % 2 == A) {
-                        al[k] = __ldg(a.fac + (long long)(a.fac_ofs + 2 * k) * V + cell);
-                        be[k] = __ldg(a.fac + (long long)(a.fac_ofs + 2 * k + 1) * V + cell) * a.inv_h;
+                for (int par = 0; par < 2; ++par) {
+                    const int gx = ((par == 0) == (T == 0)) ? 0 : 1;
+                    const int gz = ((A + par) & 1) == 0 ? 0 : 1;
+                    const int gc = gx + 2 * T + 4 * gz;
+                    const float al = __ldg(a.fac + (long long)(a.fac_ofs + 2 * gc) * V + cell);
+                    const float be = __ldg(a.fac + (long long)(a.fac_ofs + 2 * gc + 1) * V + cell) * a.inv_h;
+                    if (par == 0) {
+                        alE = al;
+                        beE = be;
+                    } else {
+                        alO = al;
+                        beO = be;
                     }
                 }
-                if (A == 0) {
+                if (A == 0 && T == 0) {
                     al0 = __ldg(a.fac + (long long)FAC_U0 * V + cell);
                     be0 = __ldg(a.fac + (long long)(FAC_U0 + 1) * V + cell) * a.inv_h;
                     ga0 = __ldg(a.fac + (long long)(FAC_U0 + 2) * V + cell);
                 }
             }
         }
-        const unsigned bar = (s & 1) ? bar1 : bar0;
-        const bool ok = wait_phase(bar, (unsigned)((s >> 1) & 1), a.wait_limit);
-        if (__syncthreads_or(!ok)) {
-            fail_at = s;
-#ifdef RTPN_STAGE_CHECKS
-            if (tid == 0) atomicCAS(a.status + 5, 0u, (unsigned)(s + 1));
-#endif
+        const bool fin = active && i >= 1 && (T == 0 || i - 1 >= 1);  // target column i - 1 of type T
+
+        if (!__all_sync(0xffffffffu, wait_phase(full0 + 8 * b, ph, a.wait_limit))) {
+            if (lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
             break;
         }
-        if (tid == 0) RTPN_SCOUNT(4);
-        if (tid < 32 && s + 1 < total) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (i + 1 < NSTAGE) {
-                issue(s + 1, i + 1, g);
-            } else {
-                const TileGeo gn = tile_geo<TX, TY, TZ, HX>(a, cur_tile + gridDim.x);
-                issue(s + 1, 0, gn);
-            }
-        }
-        const unsigned char* buf = bufs + (s & 1) * L::BUF;
+        const unsigned char* buf = bufs + b * L::BUF;
 
-        if (active && i <= N) {
+        if (active && column_len(N, i, B) > 0) {
             // ---- scatter source column i into prev (i-1), cur (i), next (i+1)
             const int Ms = i;
-            const int dz = ((B + Ms) & 1) == 0 ? 1 : -1;
-            const bool inz = lz + dz >= 0 && lz + dz < g.wz;
-            const int fq = first_l(Ms, B) / 2;  // component q' = q - fq inside a run's boxes
-            static_for<2>([&](auto ti) {
-                constexpr int ts = decltype(ti)::value;
-                if (ts == 1 && Ms == 0) return;
-                const unsigned char* rb = buf + ts * L::SRC_T;
-                const int dx = dir_x(Ms, ts);
+            const int fq = first_l(Ms, B) / 2;  // run slot of source q is q - fq
+            const float* cf = reinterpret_cast<const float*>(buf + L::COEFO);
+            static_for<2>([&](auto Ti) {
+                constexpr int TT = decltype(Ti)::value;
+                if (T != TT) return;
+                constexpr int O = 1 - TT;                  // the other type
+                const int dz = ((B + Ms) & 1) == 0 ? 1 : -1;
+                const bool inz = lz + dz >= 0 && lz + dz < g.wz;
+                const int dx = dir_x(Ms, TT);
                 const bool inx = lx + dx >= 0 && lx + dx < g.wx;
-                constexpr int dy = ts == 0 ? 1 : -1;
-                // per neighbour: address of component q' = 0 and the stride between components
+                constexpr int dy = O == 0 ? 1 : -1;        // the other type's y partner
+                const bool iny = ly + dy >= 0 && ly + dy < g.wy;
+                const unsigned char* rb = buf + TT * L::SRC_T;
+                const unsigned char* ro = buf + O * L::SRC_T;
+                // per neighbour: address of run slot -fq (so source q sits at q) and the slot stride
                 const unsigned char* pc = rb + my - fq * L::CTR_BYTES;
                 const unsigned char* px =
                     inx ? pc + dx * L::ES
                         : rb + L::HXO + ((lz * TY + ly) * HX + (dx > 0 ? g.hx_elem[1] : g.hx_elem[0])) * L::ES -
                               fq * L::HX_BYTES;
                 const int sx = inx ? L::CTR_BYTES : L::HX_BYTES;
-                const unsigned char* py =
-                    iny[ts] ? pc + dy * TX * L::ES : rb + L::HYO + (lz * TX + lx) * L::ES - fq * L::HY_BYTES;
-                const int sy = iny[ts] ? L::CTR_BYTES : L::HY_BYTES;
                 const unsigned char* pz =
                     inz ? pc + dz * TX * TY * L::ES : rb + L::HZO + (ly * TX + lx) * L::ES - fq * L::HZ_BYTES;
                 const int sz = inz ? L::CTR_BYTES : L::HZ_BYTES;
-                // local index of slot (ts, q) is cbase + q
-                const int cbase = colB[Ms] + ts * column_len(N, Ms, B) - fq;
-                static_for<SPLIT>([&](auto pi) {
-                constexpr int P = decltype(pi)::value;
-                constexpr int QLO = P * NLP, QHI = (P + 1) * NLP < NL ? (P + 1) * NLP : NL;
-                if (part != P) return;
-                static_for<NL>([&](auto qi) {
-                    constexpr int q = decltype(qi)::value;
-                    constexpr int ls = 2 * q + B;
-                    constexpr int lm = (ls - 1) / 2, lp = (ls + 1) / 2;  // acc index of l-1, l+1
-                    constexpr bool has_m = ls - 1 >= 0 && lm >= QLO && lm < QHI;
-                    constexpr bool has_p = ls + 1 <= N && lp >= QLO && lp < QHI;
-                    if constexpr (ls <= N && (has_m || has_p)) {
-                        if (ls < Ms) return;
-                        if (!RTPN_SCHECK(q - fq >= 0 && q - fq < NL && cbase + q >= 0 &&
-                                         cbase + q < class_size(N, B)))
-                            return;
-                        const float c = lds<S>(pc, q * L::CTR_BYTES);
-                        const float ddx = lds<S>(px, q * sx) - c;
-                        const float ddy = lds<S>(py, q * sy) - c;
-                        const float ddz = lds<S>(pz, q * sz) - c;
-                        const float4* cf = reinterpret_cast<const float4*>(coef + (cbase + q) * CPAD);
-                        const float4 k0 = cf[0], k1 = cf[1], k2 = cf[2];
-                        constexpr int am = has_m ? lm - QLO : 0, ap = has_p ? lp - QLO : 0;
-                        if constexpr (has_m) cur[ts][am] = fmaf(k0.x, ddz, cur[ts][am]);
-                        if constexpr (has_p) cur[ts][ap] = fmaf(k0.y, ddz, cur[ts][ap]);
-                        if constexpr (has_m) prev[ts][am] = fmaf(k0.z, ddx, prev[ts][am]);
-                        if constexpr (has_p) prev[ts][ap] = fmaf(k0.w, ddx, prev[ts][ap]);
-                        if constexpr (has_m) next[ts][am] = fmaf(k1.x, ddx, next[ts][am]);
-                        if constexpr (has_p) next[ts][ap] = fmaf(k1.y, ddx, next[ts][ap]);
-                        if constexpr (has_m) prev[1 - ts][am] = fmaf(k1.z, ddy, prev[1 - ts][am]);
-                        if constexpr (has_p) prev[1 - ts][ap] = fmaf(k1.w, ddy, prev[1 - ts][ap]);
-                        if constexpr (has_m) next[1 - ts][am] = fmaf(k2.x, ddy, next[1 - ts][am]);
-                        if constexpr (has_p) next[1 - ts][ap] = fmaf(k2.y, ddy, next[1 - ts][ap]);
-                    }
-                });
-                });
+                const unsigned char* po = ro + my - fq * L::CTR_BYTES;
+                const unsigned char* py =
+                    iny ? po + dy * TX * L::ES : ro + L::HYO + (lz * TX + lx) * L::ES - fq * L::HY_BYTES;
+                const int sy = iny ? L::CTR_BYTES : L::HY_BYTES;
+                const float4* cown = reinterpret_cast<const float4*>(cf + (TT * L::NLC - fq) * CPAD);
+                const float4* coth = reinterpret_cast<const float4*>(cf + (O * L::NLC - fq) * CPAD);
+                // sources q = fq .. NLB - 1 (q < fq has l < Ms: not in the column)
+                auto sweep = [&](auto own_c, auto oth_c) {
+                    constexpr bool OWN = decltype(own_c)::value, OTH = decltype(oth_c)::value;
+                    auto slot = [&](auto qi) {
+                        constexpr int q = decltype(qi)::value;
+                        if constexpr (q < NLB) {
+                            constexpr int ls = 2 * q + B;
+                            constexpr int lm = (ls - 1) / 2, lp = (ls + 1) / 2;  // acc index of l-1, l+1
+                            constexpr bool has_m = ls - 1 >= 0 && lm < NLA;
+                            constexpr bool has_p = ls + 1 <= N && lp < NLA;
+                            if constexpr (has_m || has_p) {
+                                if (!RTPN_SCHECK(q - fq >= 0 && q - fq < column_len(N, Ms, B))) return;
+                                constexpr int am = has_m ? lm : 0, ap = has_p ? lp : 0;
+                                if constexpr (OWN) {
+                                    const float c = lds<S>(pc, q * L::CTR_BYTES);
+                                    const float ddx = lds<S>(px, q * sx) - c;
+                                    const float ddz = lds<S>(pz, q * sz) - c;
+                                    const float4 k0 = cown[3 * q], k1 = cown[3 * q + 1];
+                                    if constexpr (has_m) cur[am] = fmaf(k0.x, ddz, cur[am]);
+                                    if constexpr (has_p) cur[ap] = fmaf(k0.y, ddz, cur[ap]);
+                                    if constexpr (has_m) prev[am] = fmaf(k0.z, ddx, prev[am]);
+                                    if constexpr (has_p) prev[ap] = fmaf(k0.w, ddx, prev[ap]);
+                                    if constexpr (has_m) next[am] = fmaf(k1.x, ddx, next[am]);
+                                    if constexpr (has_p) next[ap] = fmaf(k1.y, ddx, next[ap]);
+                                }
+                                if constexpr (OTH) {
+                                    const float c = lds<S>(po, q * L::CTR_BYTES);
+                                    const float ddy = lds<S>(py, q * sy) - c;
+                                    const float4 k2 = coth[3 * q + 2];
+                                    if constexpr (has_m) prev[am] = fmaf(k2.x, ddy, prev[am]);
+                                    if constexpr (has_p) prev[ap] = fmaf(k2.y, ddy, prev[ap]);
+                                    if constexpr (has_m) next[am] = fmaf(k2.z, ddy, next[am]);
+                                    if constexpr (has_p) next[ap] = fmaf(k2.w, ddy, next[ap]);
+                                }
+                            }
+                        }
+                    };
+                    switch (fq) { RTPN_SLOT_CASES(slot) }
+                };
+                // at |m| = 0 only the cos type exists
+                if (Ms == 0)
+                    sweep(std::integral_constant<bool, TT == 0>{}, std::integral_constant<bool, O == 0>{});
+                else
+                    sweep(std::true_type{}, std::true_type{});
             });
         }
-        if (active && i >= 1) {
-            // ---- finish target column i - 1 (its accumulators are in prev)
+        if (fin) {
+            // ---- finish target column M = i - 1 (its accumulators are in prev), Eq. (5); the old
+            // values are the column's tile boxes in this stage
             const int M = i - 1;
-            static_for<2>([&](auto ti) {
-                constexpr int t = decltype(ti)::value;
-                if (t == 1 && M == 0) return;
-                // slot of (l, M, t) for l of class A: x by (M, t), y by t, z by (A + M)
-                const int gx = (((M & 1) == 0) == (t == 0)) ? 0 : 1;
-                const int gz = ((A + M) & 1) == 0 ? 0 : 1;
-                const int gcode = gx + 2 * t + 4 * gz;
-                float alpha = 0.f, beta = 0.f;
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (k == gcode) {
-                        alpha = al[k];
-                        beta = be[k];
-                    }
-                S* tptr = reinterpret_cast<S*>(a.u) +
-                          (long long)(cA0 + colA[M] + t * column_len(N, M, A) - first_l(M, A) / 2) * V +
-                          cell;
-                static_for<SPLIT>([&](auto pi) {
-                constexpr int P = decltype(pi)::value;
-                constexpr int QLO = P * NLP, QHI = (P + 1) * NLP < NL ? (P + 1) * NLP : NL;
-                if (part != P) return;
-                static_for<NL>([&](auto qi) {
-                    constexpr int q = decltype(qi)::value;
-                    constexpr int l = 2 * q + A;
-                    if constexpr (l <= N && q >= QLO && q < QHI) {
-                        if (l < M) return;
-                        const long long gi = (long long)(cA0 + colA[M] + t * column_len(N, M, A) -
-                                                         first_l(M, A) / 2 + q);
-                        if (!RTPN_SCHECK(gi >= cA0 && gi < a.nc && cell >= 0 && cell < V)) return;
-                        const float old =
-                            lds<S>(buf + L::TGT0 + t * L::R_CTR, my + (q - first_l(M, A) / 2) * L::CTR_BYTES);
-                        const float r = prev[t][q - QLO];
-                        float nv;
-                        if (A == 0 && l == 0 && M == 0)
-                            nv = fmaf(al0, old, fmaf(-be0, r, ga0));
-                        else
-                            nv = fmaf(alpha, old, -beta * r);
-                        win::store<S>(tptr + (long long)q * V, nv);
-                    }
-                });
-                });
-            });
+            const float alpha = (M & 1) ? alO : alE, beta = (M & 1) ? beO : beE;
+            S* tp = tgt_ptr(M);
+            (void)RTPN_SCHECK(offA == colA[M]);
+            const int q0 = first_l(M, A) / 2;  // targets q = q0 .. NLA - 1 (l >= M)
+            const unsigned char* ob = buf + L::TGTO + T * L::R_TGT + my - q0 * L::CTR_BYTES;
+            auto tslot = [&](auto qi) {
+                constexpr int q = decltype(qi)::value;
+                if constexpr (q < NLA) {
+                    const float old = lds<S>(ob, q * L::CTR_BYTES);
+                    float nv;
+                    if (A == 0 && q == 0 && M == 0)
+                        nv = fmaf(al0, old, fmaf(-be0, prev[q], ga0));
+                    else
+                        nv = fmaf(alpha, old, -beta * prev[q]);
+                    win::store<S>(tp + (long long)q * V, nv);
+                }
+            };
+            switch (q0) { RTPN_SLOT_CASES(tslot) }
         }
-        // shift the window: prev <- cur <- next <- 0 (also resets a finished tile)
-#pragma unroll
-        for (int t = 0; t < 2; ++t)
-#pragma unroll
-            for (int q = 0; q < NLP; ++q) {
-                prev[t][q] = cur[t][q];
-                cur[t][q] = next[t][q];
-                next[t][q] = 0.f;
-            }
-        if (i == NSTAGE - 1) {
-#pragma unroll
-            for (int t = 0; t < 2; ++t)
-#pragma unroll
-                for (int q = 0; q < NLP; ++q) prev[t][q] = cur[t][q] = 0.f;
+        // the stage buffer is free once every lane of the warp is past its reads
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8 * b);
+        if (++b == NB) {
+            b = 0;
+            ph ^= 1u;
         }
-        // No barrier here: buffer s & 1 is refilled by the issue of stage s + 2, which warp 0 makes
-        // only after the barrier of stage s + 1's wait, when every thread is done with stage s.
-    }
-
-    if (fail_at >= 0) {
-        if (tid == 0) atomicOr(a.status, STATUS_TIMEOUT);
-        // Only the copies of the stage that timed out can still be in flight (the next stage is
-        // issued after a successful wait); give them one more bounded wait before leaving.
-        wait_phase((fail_at & 1) ? bar1 : bar0, (unsigned)((fail_at >> 1) & 1), a.wait_limit);
-        __syncthreads();
+        // shift the window: prev <- cur <- next <- 0
+#pragma unroll
+        for (int q = 0; q < NLA; ++q) {
+            prev[q] = cur[q];
+            cur[q] = next[q];
+            next[q] = 0.f;
+        }
+        if (i >= 1) offA += ntypes(i - 1) * column_len(N, i - 1, A);
+        if (i == NST - 1) {  // tile done: reset the window and the column offset
+#pragma unroll
+            for (int q = 0; q < NLA; ++q) prev[q] = cur[q] = 0.f;
+            offA = 0;
+        }
     }
 }
 

@@ -33,7 +33,7 @@ class Info(ctypes.Structure):
                 ("nz", ctypes.c_int), ("bc", ctypes.c_int), ("precision", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("h", ctypes.c_double), ("dt", ctypes.c_double),
                 ("state_bytes", ctypes.c_size_t), ("factor_bytes", ctypes.c_size_t),
-                ("steps_done", ctypes.c_longlong), ("tile", ctypes.c_int * 3), ("chunks", ctypes.c_int)]
+                ("steps_done", ctypes.c_longlong), ("tile", ctypes.c_int * 3), ("depth", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -203,8 +203,8 @@ class Context:
         handle = getattr(stream, "cuda_stream", stream)
         self._chk(lib().rtpn_set_stream(self._p, _P(handle or 0)))
 
-    def set_kernel(self, kernel: str = "auto", tile=(0, 0, 0), chunks: int = 0):
-        self._chk(lib().rtpn_set_kernel_ex(self._p, KERNEL[kernel], *tile, int(chunks)))
+    def set_kernel(self, kernel: str = "auto", tile=(0, 0, 0), depth: int = 0):
+        self._chk(lib().rtpn_set_kernel_ex(self._p, KERNEL[kernel], *tile, int(depth)))
 
     def autotune(self, reps: int = 2):
         """Time candidate window-kernel tiles on this context's data, apply the best; (tile, ms)."""

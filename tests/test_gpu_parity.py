@@ -215,28 +215,29 @@ def test_autotune_keeps_state_and_picks_a_valid_tile(cuda_device, coupling_cache
 
 
 STAGE_CASES = [
-    # N, shape (nz, ny, nx) with nx a multiple of 8, bc, tile (0 = default), threads per cell
+    # N, shape (nz, ny, nx) with nx a multiple of 8, bc, tile (0 = default), stage buffers (0 = any)
     (7, (9, 13, 72), "vacuum", (0, 0, 0), 0),
     (7, (5, 6, 32), "periodic", (0, 0, 0), 0),
-    (15, (7, 9, 40), "periodic", (32, 4, 2), 2),
-    (15, (3, 5, 8), "vacuum", (32, 4, 2), 1),
-    (39, (5, 6, 8), "periodic", (32, 2, 2), 2),
-    (39, (5, 7, 8), "vacuum", (40, 2, 2), 4),
-    (39, (3, 5, 80), "periodic", (40, 2, 2), 1),
-    (39, (4, 3, 72), "vacuum", (40, 2, 2), 2),
+    (15, (7, 9, 40), "periodic", (32, 4, 2), 4),
+    (15, (3, 5, 8), "vacuum", (32, 4, 2), 0),
+    (39, (5, 6, 8), "periodic", (32, 2, 2), 3),
+    (39, (5, 7, 8), "vacuum", (40, 2, 2), 2),
+    (39, (3, 5, 80), "periodic", (40, 2, 2), 2),
+    (39, (4, 3, 72), "vacuum", (40, 2, 2), 0),
+    (39, (7, 5, 120), "periodic", (40, 2, 2), 2),
 ]
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
-@pytest.mark.parametrize("N,shape,bc,tile,chunks", STAGE_CASES)
-def test_stage_kernel(cuda_device, coupling_cache, N, shape, bc, tile, chunks, precision):
-    # TMA-staged kernel: full and partial tiles, wrapped and zero-filled halos, component chunks
+@pytest.mark.parametrize("N,shape,bc,tile,depth", STAGE_CASES)
+def test_stage_kernel(cuda_device, coupling_cache, N, shape, bc, tile, depth, precision):
+    # TMA-staged kernel: full and partial tiles, wrapped and zero-filled halos, pipeline depths
     inst, u0 = synth.random_instance(N, shape, seed=300 + N, bc=bc)
     ref = oracle_problem(inst, coupling_cache).run(u0, 3)
     with rtpn.Context(N, inst.shape, inst.h, inst.bc, precision, inst.dt) as ctx:
-        ctx.set_kernel("stage", tile, chunks)
+        ctx.set_kernel("stage", tile, depth)
         info = ctx.info()
-        assert info.kernel == 3 and (chunks == 0 or info.chunks == chunks)
+        assert info.kernel == 3 and (depth == 0 or info.depth == depth)
         ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
         ctx.set_moments(u0)
         ctx.step(3)
