@@ -277,7 +277,8 @@ int rtpn_batch_autotune(rtpn_batch* b, int reps, int tile[3], double* ms);
 int rtpn_synchronize(rtpn_ctx* ctx);
 
 /* Test hook for the timeout path: one staged pass of class cls in which one stage's copies are
- * deliberately never issued, with `wait_limit` mbarrier polls, so every CTA's bounded wait must run
+ * deliberately never issued, with `wait_limit` mbarrier polls (each sleeps up to 2 us), so every
+ * CTA's bounded wait must run
  * out, set the status word and leave.  The next rtpn_synchronize returns RTPN_ETIMEOUT.  Leaves the
  * state undefined.  RTPN_EUNSUPPORTED unless the staged kernel is active. */
 int rtpn_test_wait_timeout(rtpn_ctx* ctx, int cls, long long wait_limit);

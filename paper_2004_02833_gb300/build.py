@@ -32,7 +32,7 @@ def _nvcc() -> str:
 
 
 VARIANT_SRC = "window.cu"  # compiled once per (order, class) listed in window_variants.h
-STAGE_SRC = "stage.cu"     # compiled once per (order, tile, depth) listed in stage_variants.h
+STAGE_SRC = "stage.cu"     # compiled once per (order, tile, depth, box size) listed in stage_variants.h
 
 
 def window_orders() -> list[int]:
@@ -41,11 +41,11 @@ def window_orders() -> list[int]:
     return [int(v) for v in re.findall(r"X\((\d+)\)", line)]
 
 
-def stage_variants() -> list[tuple[int, int, int, int, int]]:
+def stage_variants() -> list[tuple[int, int, int, int, int, int]]:
     text = open(os.path.join(CSRC, "stage_variants.h")).read()
     line = [l for l in text.splitlines() if l.startswith("#define RTPN_STAGE_VARIANTS")][0]
     return [tuple(int(v) for v in m) for m in
-            re.findall(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", line)]
+            re.findall(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", line)]
 
 
 def units() -> list[tuple[str, list[str], str]]:
@@ -59,11 +59,11 @@ def units() -> list[tuple[str, list[str], str]]:
         for cls in (0, 1):
             out.append((os.path.join(CSRC, VARIANT_SRC), [f"-DRTPN_WN={n}", f"-DRTPN_WCLS={cls}"],
                         f"window_N{n}_c{cls}.o"))
-    for n, tx, ty, tz, nb in stage_variants():
+    for n, tx, ty, tz, nb, em in stage_variants():
         out.append((os.path.join(CSRC, STAGE_SRC),
                     [f"-DRTPN_SN={n}", f"-DRTPN_STX={tx}", f"-DRTPN_STY={ty}", f"-DRTPN_STZ={tz}",
-                     f"-DRTPN_SNB={nb}"],
-                    f"stage_N{n}_{tx}x{ty}x{tz}_b{nb}.o"))
+                     f"-DRTPN_SNB={nb}", f"-DRTPN_SEM={em}"],
+                    f"stage_N{n}_{tx}x{ty}x{tz}_b{nb}_e{em}.o"))
     return out
 
 

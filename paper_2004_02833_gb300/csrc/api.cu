@@ -296,7 +296,7 @@ int choose_kernel(rtpn_ctx* ctx) {
     if (k == RTPN_KERNEL_AUTO) {
         const bool tile_set = ctx->tx || ctx->ty || ctx->tz;
         if (kStageInAuto && stage_supported(ctx->N, ctx->prec, ctx->g.nx) &&
-            (!tile_set || stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->depth)))
+            (!tile_set || stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->depth, ctx->prec)))
             k = RTPN_KERNEL_STAGE;
         else
             k = window_supported(ctx->N, ctx->prec) ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
@@ -305,7 +305,7 @@ int choose_kernel(rtpn_ctx* ctx) {
         if (!stage_supported(ctx->N, ctx->prec, ctx->g.nx))
             return fail(ctx, RTPN_EUNSUPPORTED,
                         "staged kernel not compiled for this N/precision or nx*elem not 16-byte rows");
-        if (!stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->depth))
+        if (!stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->depth, ctx->prec))
             return fail(ctx, RTPN_EUNSUPPORTED, "no staged kernel compiled for this tile / stage depth");
         int rc = stage_prepare(ctx, ctx->tx, ctx->ty, ctx->tz, ctx->depth);
         if (rc) return fail(ctx, RTPN_ECUDA, std::string("staged kernel set-up: ") +

@@ -130,7 +130,7 @@ int rtpn_autotune(rtpn_ctx* ctx, int reps, int tile[3], double* ms_per_step) {
     std::vector<Tile> cands;
     if (kernel == RTPN_KERNEL_STAGE) {
         int v[4 * 64];
-        const int n = rtpn::stage_variants_of(ctx->N, v, 64);
+        const int n = rtpn::stage_variants_of(ctx->N, ctx->prec, v, 64);
         for (int i = 0; i < n; ++i) cands.push_back({v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]});
     } else {
         for (const Tile& t : kCandidates) cands.push_back(t);

@@ -11,9 +11,10 @@
 namespace rtpn {
 namespace stg {
 
-#define RTPN_SDECL(n, x, y, z, b)                                                                  \
-    int stage_launch_##n##_##x##_##y##_##z##_##b(int, int, const Args&, int, cudaStream_t);          \
-    int stage_smem_##n##_##x##_##y##_##z##_##b(int, int);
+#define RTPN_SDECL(n, x, y, z, b, e)                                                                 \
+    int stage_launch_##n##_##x##_##y##_##z##_##b##_##e(int, int, const Args&, int, cudaStream_t);       \
+    int stage_smem_##n##_##x##_##y##_##z##_##b##_##e(int, int);                                          \
+    int stage_boxcomps_##n##_##x##_##y##_##z##_##b##_##e(int);
 RTPN_STAGE_VARIANTS(RTPN_SDECL)
 #undef RTPN_SDECL
 
@@ -21,17 +22,22 @@ struct Variant {
     int N, tx, ty, tz, depth;
     int (*launch)(int, int, const Args&, int, cudaStream_t);
     int (*smem)(int, int);
+    int (*boxcomps)(int);
 };
-#define RTPN_SENTRY(n, x, y, z, b)                                                      \
-    Variant{n, x, y, z, b, stage_launch_##n##_##x##_##y##_##z##_##b, stage_smem_##n##_##x##_##y##_##z##_##b},
+#define RTPN_SENTRY(n, x, y, z, b, e)                                                                \
+    Variant{n, x, y, z, b, stage_launch_##n##_##x##_##y##_##z##_##b##_##e,                           \
+            stage_smem_##n##_##x##_##y##_##z##_##b##_##e, stage_boxcomps_##n##_##x##_##y##_##z##_##b##_##e},
 static const Variant kVariants[] = {RTPN_STAGE_VARIANTS(RTPN_SENTRY)};
 #undef RTPN_SENTRY
 
-// first compiled variant of order N with this tile (0 = any) and depth (0 = any)
-static const Variant* find(int N, int tx, int ty, int tz, int depth = 0) {
+// a variant is usable for a storage precision if its stage ring fits shared memory
+static bool fits(const Variant& v, int precision) { return v.smem(0, precision) > 0 && v.smem(1, precision) > 0; }
+
+// first compiled variant of order N with this tile (0 = any) and depth (0 = any) that fits
+static const Variant* find(int N, int tx, int ty, int tz, int depth, int precision) {
     for (const auto& v : kVariants)
         if (v.N == N && (tx == 0 || (v.tx == tx && v.ty == ty && v.tz == tz)) &&
-            (depth == 0 || v.depth == depth))
+            (depth == 0 || v.depth == depth) && fits(v, precision))
             return &v;
     return nullptr;
 }
@@ -68,22 +74,23 @@ static bool make_map(CUtensorMap* m, void* base, int precision, const rtpn::Geom
 }  // namespace stg
 
 bool stage_supported(int N, int precision, int nx) {
-    if (precision == RTPN_FP64 || !stg::find(N, 0, 0, 0)) return false;
+    if (precision == RTPN_FP64 || !stg::find(N, 0, 0, 0, 0, precision)) return false;
     const int hx = precision == RTPN_BF16 ? 8 : 4;  // 16-byte rows for the tensor maps
     return nx % hx == 0;
 }
 
-bool stage_has_tile(int N, int tx, int ty, int tz, int depth) {
-    return stg::find(N, tx, ty, tz, depth) != nullptr;
+bool stage_has_tile(int N, int tx, int ty, int tz, int depth, int precision) {
+    return stg::find(N, tx, ty, tz, depth, precision) != nullptr;
 }
 
 int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
-    const stg::Variant* v = stg::find(ctx->N, tx, ty, tz, depth);
+    const stg::Variant* v = stg::find(ctx->N, tx, ty, tz, depth, ctx->prec);
     if (!v) return (int)cudaErrorNotSupported;
     // default (no tile given): the first listed variant whose width divides nx, else the first one
     if (tx == 0)
         for (const auto& w : stg::kVariants)
-            if (w.N == ctx->N && (depth == 0 || w.depth == depth) && ctx->g.nx % w.tx == 0) {
+            if (w.N == ctx->N && (depth == 0 || w.depth == depth) && ctx->g.nx % w.tx == 0 &&
+                stg::fits(w, ctx->prec)) {
                 v = &w;
                 break;
             }
@@ -93,7 +100,7 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
     // the four tensor maps live in device global memory (64-byte aligned) and the kernel reads
     // them from there: tile box, x-halo group, y-halo row, z-halo plane, each spanning E consecutive
     // components of a (type, |m|) run
-    const int e = stg::box_comps(N, v->tx, v->ty, v->tz, es);
+    const int e = v->boxcomps(ctx->prec);
     if (e <= 0) return (int)cudaErrorInvalidValue;
     alignas(64) CUtensorMap maps[4];
     if (!stg::make_map(&maps[0], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, v->tz, e) ||
@@ -160,10 +167,10 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
 }
 
 // the compiled (tile, depth) choices of order N, for the tuner
-int stage_variants_of(int N, int* tiles, int max) {
+int stage_variants_of(int N, int precision, int* tiles, int max) {
     int n = 0;
     for (const auto& v : stg::kVariants)
-        if (v.N == N && n < max) {
+        if (v.N == N && stg::fits(v, precision) && n < max) {
             tiles[4 * n] = v.tx;
             tiles[4 * n + 1] = v.ty;
             tiles[4 * n + 2] = v.tz;
@@ -206,7 +213,7 @@ int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long
     a.maps = (const CUtensorMap*)ctx->stage_maps_dev;
     a.nc = ctx->md.nc;
     a.status = ctx->status;
-    a.wait_limit = wait_limit;
+    a.wait_limit = (unsigned)(wait_limit > 0xffffffffll ? 0xffffffffll : wait_limit);
     a.skip_stage = skip_stage;
     return v.launch(cls, ctx->prec, a, ctx->sms, st);
 }

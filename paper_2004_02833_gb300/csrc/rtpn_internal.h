@@ -86,15 +86,16 @@ HostTable transposed_table(const Model& md, int clsB, double h);
 // ---- TMA-staged kernels (kernels_stage.cu, stage.cu) ----
 // nx must give 16-byte rows for the tensor maps
 bool stage_supported(int N, int precision, int nx);
-bool stage_has_tile(int N, int tx, int ty, int tz, int depth);
+bool stage_has_tile(int N, int tx, int ty, int tz, int depth, int precision);
 // builds the tensor maps (tile 0,0,0 = default; depth 0 = any) and the coupling tables;
 // returns cudaError_t
 int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth);
-// compiled (tx, ty, tz, depth) of order N into tiles[4*i..]; returns the count
-int stage_variants_of(int N, int* tiles, int max);
+// compiled (tx, ty, tz, depth) of order N that fit for this precision into tiles[4*i..];
+// returns the count
+int stage_variants_of(int N, int precision, int* tiles, int max);
 int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long skip_stage,
                  long long wait_limit);
-constexpr long long STAGE_WAIT_LIMIT = 1ll << 22;  // mbarrier polls before a wait gives up
+constexpr long long STAGE_WAIT_LIMIT = 1ll << 20;  // mbarrier polls (each <= 2 us) before a wait gives up
 
 }  // namespace rtpn
 

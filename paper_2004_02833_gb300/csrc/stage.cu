@@ -1,15 +1,17 @@
 // One variant of the TMA-staged substep kernel: order RTPN_SN, CTA tile RTPN_STX x RTPN_STY x
-// RTPN_STZ, RTPN_SNB stage buffers, both target classes, FP32 and BF16 storage.  kernels_stage.cu
+// RTPN_STZ, RTPN_SNB stage buffers, at least RTPN_SEM components per TMA box, both target classes,
+// FP32 and BF16 storage.  kernels_stage.cu
 // dispatches to it.
 #include "stage_impl.cuh"
 
-#if !defined(RTPN_SN) || !defined(RTPN_STX) || !defined(RTPN_STY) || !defined(RTPN_STZ) || !defined(RTPN_SNB)
-#error "compile with -DRTPN_SN=<order> -DRTPN_STX=.. -DRTPN_STY=.. -DRTPN_STZ=.. -DRTPN_SNB=.."
+#if !defined(RTPN_SN) || !defined(RTPN_STX) || !defined(RTPN_STY) || !defined(RTPN_STZ) || !defined(RTPN_SNB) || \
+    !defined(RTPN_SEM)
+#error "compile with -DRTPN_SN=<order> -DRTPN_STX=.. -DRTPN_STY=.. -DRTPN_STZ=.. -DRTPN_SNB=.. -DRTPN_SEM=.."
 #endif
 
-#define RTPN_SCAT2(a, b, c, d, e, f) a##_##b##_##c##_##d##_##e##_##f
-#define RTPN_SCAT(a, b, c, d, e, f) RTPN_SCAT2(a, b, c, d, e, f)
-#define RTPN_SVARIANT(name) RTPN_SCAT(name, RTPN_SN, RTPN_STX, RTPN_STY, RTPN_STZ, RTPN_SNB)
+#define RTPN_SCAT2(a, b, c, d, e, f, g) a##_##b##_##c##_##d##_##e##_##f##_##g
+#define RTPN_SCAT(a, b, c, d, e, f, g) RTPN_SCAT2(a, b, c, d, e, f, g)
+#define RTPN_SVARIANT(name) RTPN_SCAT(name, RTPN_SN, RTPN_STX, RTPN_STY, RTPN_STZ, RTPN_SNB, RTPN_SEM)
 
 namespace rtpn {
 namespace stg {
@@ -18,18 +20,22 @@ namespace stg {
 // defines a k_stage / launch_one of the same name, and the linker must not merge them.
 namespace {
 
-constexpr int kN = RTPN_SN, kTX = RTPN_STX, kTY = RTPN_STY, kTZ = RTPN_STZ, kNB = RTPN_SNB;
-constexpr int kThreads = Layout<kN, 0, float, kTX, kTY, kTZ, kNB>::THREADS;
+constexpr int kN = RTPN_SN, kTX = RTPN_STX, kTY = RTPN_STY, kTZ = RTPN_STZ, kNB = RTPN_SNB, kEM = RTPN_SEM;
+constexpr int kThreads = Layout<kN, 0, float, kTX, kTY, kTZ, kNB, kEM>::THREADS;
 
 template <int A, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_stage(Args a) {
+    static_assert(Layout<kN, A, S, kTX, kTY, kTZ, kNB, kEM>::FITS, "stage ring exceeds shared memory");
     extern __shared__ __align__(128) unsigned char smem[];
-    stage_kernel_body<kN, A, S, kTX, kTY, kTZ, kNB>(a, smem);
+    stage_kernel_body<kN, A, S, kTX, kTY, kTZ, kNB, kEM>(a, smem);
 }
 
 template <int A, typename S>
 int launch_one(const Args& a, int sms, cudaStream_t st) {
-    using L = Layout<kN, A, S, kTX, kTY, kTZ, kNB>;
+    using L = Layout<kN, A, S, kTX, kTY, kTZ, kNB, kEM>;
+    if constexpr (!L::FITS) {
+        return (int)cudaErrorNotSupported;  // this depth is compiled for the narrower storage only
+    } else {
     static bool configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -49,6 +55,7 @@ int launch_one(const Args& a, int sms, cudaStream_t st) {
     if (grid < 1) return 0;
     k_stage<A, S><<<(unsigned)grid, kThreads, L::BYTES, st>>>(a);
     return (int)cudaGetLastError();
+    }
 }
 
 }  // namespace
@@ -60,11 +67,20 @@ int RTPN_SVARIANT(stage_launch)(int cls, int precision, const Args& a, int sms, 
 }
 
 // dynamic shared memory of the variant, or 0 if it does not fit a CTA
+template <int A, typename S>
+constexpr int smem_of() {
+    using L = Layout<kN, A, S, kTX, kTY, kTZ, kNB, kEM>;
+    return L::FITS ? L::BYTES : 0;
+}
+// components per TMA box of the variant for a storage precision (the host builds its maps with it)
+int RTPN_SVARIANT(stage_boxcomps)(int precision) {
+    return precision == RTPN_BF16 ? Layout<kN, 0, __nv_bfloat16, kTX, kTY, kTZ, kNB, kEM>::E
+                                  : Layout<kN, 0, float, kTX, kTY, kTZ, kNB, kEM>::E;
+}
+
 int RTPN_SVARIANT(stage_smem)(int cls, int precision) {
-    if (precision == RTPN_BF16)
-        return cls == 0 ? Layout<kN, 0, __nv_bfloat16, kTX, kTY, kTZ, kNB>::BYTES
-                        : Layout<kN, 1, __nv_bfloat16, kTX, kTY, kTZ, kNB>::BYTES;
-    return cls == 0 ? Layout<kN, 0, float, kTX, kTY, kTZ, kNB>::BYTES : Layout<kN, 1, float, kTX, kTY, kTZ, kNB>::BYTES;
+    if (precision == RTPN_BF16) return cls == 0 ? smem_of<0, __nv_bfloat16>() : smem_of<1, __nv_bfloat16>();
+    return cls == 0 ? smem_of<0, float>() : smem_of<1, float>();
 }
 
 }  // namespace stg

@@ -13,9 +13,11 @@
 //  * The column sweep is a runtime loop whose body handles one column for every l slot; the three
 //    live target columns are register arrays that shift by one column per iteration, so the body
 //    is the same for every column and fits the instruction cache.
-//  * A producer warp moves each source column into shared memory with the Tensor Memory
-//    Accelerator (cp.async.bulk.tensor): per type and box kind, boxes of E consecutive components
-//    of the (type, |m|) run, as many as the column needs.  A column stage holds, per source
+//  * A producer warp moves each source column into shared memory with the Tensor Memory Accelerator
+//    (cp.async.bulk.tensor): per type and box kind, boxes of E consecutive components of the
+//    (type, |m|) run, as many as the column needs.  The TMA unit of an SM spends on the order of
+//    60 cycles per box plus a few per box row, so boxes are large (E components) and tiles wide
+//    in x (fewer, longer rows); one producer warp issues them.  A column stage holds, per source
 //    component, the tile box plus one halo slab on the side its partners read along each axis (x:
 //    an aligned 16-byte group, y: one row, z: one plane), and the column's coupling constants (a
 //    plain bulk copy).  Periodic halos use wrapped coordinates; vacuum halos use out-of-range
@@ -84,7 +86,7 @@ struct Args {
     const CUtensorMap* maps;  // four tensor maps in global memory: tile, x halo, y halo, z halo
     int nc;                   // components (bound of the 4th tensor coordinate)
     unsigned* status;       // device status word (STATUS_TIMEOUT on a wait that ran out)
-    long long wait_limit;   // try_wait polls before giving up
+    unsigned wait_limit;    // try_wait polls (each up to WAIT_HINT_NS) before giving up
     long long skip_stage;   // stage index never issued (a wait that must run out); -1 normally
 };
 
@@ -92,13 +94,14 @@ __host__ __device__ constexpr int pad128(int bytes) { return (bytes + 127) / 128
 
 // Components per TMA box along the component axis.  A box lands at a 128-byte aligned shared-memory
 // address, so E times the bytes of one component of every box kind (tile, x halo, y halo, z halo)
-// must be a multiple of 128; among such E <= 8 the one that holds a run of N/2 + 1 in the fewest
-// slots, then in the fewest boxes, is taken.
-__host__ __device__ constexpr int box_comps(int N, int tx, int ty, int tz, int es) {
+// must be a multiple of 128; among such E in [emin, 8] the one that holds a run of N/2 + 1 in the
+// fewest slots, then in the fewest boxes, is taken (each box costs the TMA unit a fixed overhead,
+// so a variant may ask for larger boxes at the price of shared memory).
+__host__ __device__ constexpr int box_comps(int N, int tx, int ty, int tz, int es, int emin) {
     const int nl0 = N / 2 + 1;
     const int kinds[4] = {tx * ty * tz * es, (16 / es) * ty * tz * es, tx * tz * es, tx * ty * es};
     int best = 0, best_slots = 1 << 30;
-    for (int e = 8; e >= 1; --e) {
+    for (int e = 8; e >= emin; --e) {
         bool ok = true;
         for (int k = 0; k < 4; ++k) ok = ok && (e * kinds[k]) % 128 == 0;
         const int slots = (nl0 + e - 1) / e * e;
@@ -111,11 +114,11 @@ __host__ __device__ constexpr int box_comps(int N, int tx, int ty, int tz, int e
 }
 __host__ __device__ constexpr int run_slots(int N, int e) { return e > 0 ? (N / 2 + e) / e * e : 0; }
 
-template <int N, int A, typename S, int TX, int TY, int TZ, int NB>
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EM = 1>
 struct Layout {
     static constexpr int B = 1 - A;
     static constexpr int ES = (int)sizeof(S);
-    static constexpr int E = box_comps(N, TX, TY, TZ, ES);  // components per box
+    static constexpr int E = box_comps(N, TX, TY, TZ, ES, EM > N / 2 + 1 ? N / 2 + 1 : EM);  // per box
     static constexpr int NL = run_slots(N, E);              // run slots per type in shared memory
     static constexpr int NG = NL / E;                       // boxes per run, at most
     static constexpr int NLC = N / 2 + 1;                   // coupling-constant slots per type
@@ -152,7 +155,7 @@ struct Layout {
     static_assert((E * CTR_BYTES) % 128 == 0 && (E * HX_BYTES) % 128 == 0 && (E * HY_BYTES) % 128 == 0 &&
                       (E * HZ_BYTES) % 128 == 0 && BUF % 128 == 0,
                   "every box must land on a 128-byte boundary");
-    static_assert(BYTES <= 232448, "stage ring exceeds the 227 KB of shared memory of a CTA");
+    static constexpr bool FITS = BYTES <= 232448;  // 227 KB of shared memory per CTA
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -169,14 +172,17 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
 __device__ __forceinline__ void mbar_arrive(unsigned bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// One poll: the thread may sleep up to WAIT_HINT_NS for the phase to complete (it wakes when it
+// does), so a warp that waits for its data spends few issue slots on the poll loop.
+constexpr unsigned WAIT_HINT_NS = 2000;
 __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "n"(WAIT_HINT_NS)
         : "memory");
     return ok != 0;
 }
@@ -195,8 +201,8 @@ __device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigne
         : "memory");
 }
 // bounded wait on one mbarrier phase; false if it ran out
-__device__ __forceinline__ bool wait_phase(unsigned bar, unsigned parity, long long limit) {
-    for (long long i = 0; i < limit; ++i)
+__device__ __forceinline__ bool wait_phase(unsigned bar, unsigned parity, unsigned limit) {
+    for (unsigned i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -293,19 +299,20 @@ __device__ __forceinline__ TileGeo tile_geo(const Args& a, unsigned t) {
 __device__ __forceinline__ int dir_x(int M, int t) { return ((M & 1) == 0) == (t == 0) ? 1 : -1; }
 
 // The producer warp: issues the copies of every stage of this CTA's sequence into the ring.
-template <int N, int A, typename S, int TX, int TY, int TZ, int NB>
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EM>
 __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* bufs, unsigned full0,
                                                unsigned empty0, int total) {
-    using L = Layout<N, A, S, TX, TY, TZ, NB>;
+    using L = Layout<N, A, S, TX, TY, TZ, NB, EM>;
     constexpr int B = 1 - A;
     constexpr int NST = N + 2;
     constexpr int E = L::E, NG = L::NG;
     const int lane = threadIdx.x & 31;
     const int cA0 = A == 0 ? 0 : class_size(N, 0);
     const int cB0 = B == 0 ? 0 : class_size(N, 0);
-    const int* colA = a.colstart + A * (N + 2);
-    const int* colB = a.colstart + B * (N + 2);
     const CUtensorMap* maps = a.maps;
+    // first local index of source column i in class B and of target column i - 1 in class A,
+    // advanced column by column (no table loads on the producer's path)
+    int offB = 0, offA = 0;
     // the maps were written by the host before the launch; make them visible to the async proxy
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -321,6 +328,7 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
         if (i == 0 && s > 0) {
             tile += gridDim.x;
             g = tile_geo<TX, TY, TZ, L::HX>(a, tile);
+            offB = offA = 0;
         }
         const unsigned full = full0 + 8 * b;
         if (s >= NB) {  // the consumers must have released the buffer's previous stage
@@ -335,6 +343,10 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
             b = 0;
             ph ^= 1u;
         }
+        // the column offsets of stage s; advanced for the next stage before anything can skip ahead
+        const int offB_s = offB, offA_s = offA;
+        offB += ntypes(i) * column_len(N, i, B);
+        if (i >= 1) offA += ntypes(i - 1) * column_len(N, i - 1, A);
         if (s == a.skip_stage) continue;
         unsigned char* buf = bufs + bcur * L::BUF;
         const int len = column_len(N, i, B);     // sources of column i (none at i = N + 1)
@@ -354,7 +366,7 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
             if (j >= 8 * NG) {
                 const int t = (j - 8 * NG) / NG, k = j % NG;
                 if (t >= ntA || k >= nboxA) continue;
-                const int c = cA0 + colA[M] + t * lenA + k * E;
+                const int c = cA0 + offA_s + t * lenA + k * E;
                 if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 111, c)) continue;
                 tma_load_4d(smem_addr(buf + L::TGTO + t * L::R_TGT) + k * E * L::CTR_BYTES, maps, g.x0, g.y0,
                             g.z0, c, full);
@@ -362,7 +374,7 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
             }
             const int t = j / (4 * NG), kind = (j / NG) % 4, k = j % NG;
             if (t >= nt || k >= nbox) continue;
-            const int c = cB0 + colB[i] + t * len + k * E;  // first component of the box
+            const int c = cB0 + offB_s + t * len + k * E;  // first component of the box
             const unsigned d = smem_addr(buf + t * L::SRC_T);
             if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 101, c)) continue;
             if (kind == 0) {
@@ -389,9 +401,9 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
         if (r != a.skip_stage) wait_phase(full0 + 8 * (r % NB), (unsigned)((r / NB) & 1), a.wait_limit);
 }
 
-template <int N, int A, typename S, int TX, int TY, int TZ, int NB>
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EM>
 __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* smem) {
-    using L = Layout<N, A, S, TX, TY, TZ, NB>;
+    using L = Layout<N, A, S, TX, TY, TZ, NB, EM>;
     static_assert(N >= 1, "order N >= 1");
     static_assert((N + 2) / 2 <= kMaxSlots, "slot switch covers N <= 45");
     constexpr int B = 1 - A;
@@ -414,7 +426,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     const unsigned full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[NB]);
     if (tid == 0) {
         for (int b = 0; b < NB; ++b) {
-            mbar_init(full0 + 8 * b, 1);
+            mbar_init(full0 + 8 * b, 1);  // the producer's arrive.expect_tx
             mbar_init(empty0 + 8 * b, L::CONSUMER_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -424,7 +436,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     const int my_tiles = a.tiles > blockIdx.x ? (int)((a.tiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
     const int total = my_tiles * NST;
     if (warp == L::CONSUMER_WARPS) {
-        stage_producer<N, A, S, TX, TY, TZ, NB>(a, bufs, full0, empty0, total);
+        stage_producer<N, A, S, TX, TY, TZ, NB, EM>(a, bufs, full0, empty0, total);
         return;
     }
 

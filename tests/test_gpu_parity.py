@@ -225,6 +225,8 @@ STAGE_CASES = [
     (39, (3, 5, 80), "periodic", (40, 2, 2), 2),
     (39, (4, 3, 72), "vacuum", (40, 2, 2), 0),
     (39, (7, 5, 120), "periodic", (40, 2, 2), 2),
+    (39, (3, 5, 120), "periodic", (80, 2, 1), 2),
+    (39, (4, 3, 160), "vacuum", (80, 2, 1), 2),
 ]
 
 
@@ -245,6 +247,24 @@ def test_stage_kernel(cuda_device, coupling_cache, N, shape, bc, tile, depth, pr
     assert rel_err(got, ref) <= TOL[precision], rel_err(got, ref)
 
 
+def test_stage_depth_that_fits_bf16_only(cuda_device, coupling_cache):
+    # P39 40x2x2 with four stage buffers fits shared memory with BF16 storage only
+    inst, u0 = synth.random_instance(39, (5, 7, 80), seed=339, bc="periodic")
+    with rtpn.Context(39, inst.shape, inst.h, inst.bc, "fp32", inst.dt) as ctx:
+        with pytest.raises(rtpn.RtpnError) as e:
+            ctx.set_kernel("stage", (40, 2, 2), 4)
+        assert e.value.code == rtpn.EUNSUPPORTED
+    ref = oracle_problem(inst, coupling_cache).run(u0, 3)
+    with rtpn.Context(39, inst.shape, inst.h, inst.bc, "bf16", inst.dt) as ctx:
+        ctx.set_kernel("stage", (40, 2, 2), 4)
+        assert ctx.info().depth == 4
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        ctx.step(3)
+        got = ctx.get_moments()
+    assert rel_err(got, ref) <= TOL["bf16"], rel_err(got, ref)
+
+
 def test_stage_kernel_long_run_matches_window(cuda_device):
     inst, u0 = synth.random_instance(39, (6, 8, 40), seed=5, bc="periodic")
     a = gpu_run(inst, u0, 20, "fp32", kernel="stage")
@@ -261,7 +281,7 @@ def test_stage_wait_timeout_is_reported(cuda_device, coupling_cache):
         ctx.set_kernel("stage")
         ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
         ctx.set_moments(u0)
-        assert rtpn.lib().rtpn_test_wait_timeout(ctx._p, 0, 2000) == rtpn.OK
+        assert rtpn.lib().rtpn_test_wait_timeout(ctx._p, 0, 200) == rtpn.OK
         with pytest.raises(rtpn.RtpnError) as e:
             ctx.synchronize()
         assert e.value.code == rtpn.ETIMEOUT
