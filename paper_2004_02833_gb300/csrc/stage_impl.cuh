@@ -514,11 +514,12 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                 if (T != TT) return;
                 constexpr int O = 1 - TT;                  // the other type
                 const int dz = ((B + Ms) & 1) == 0 ? 1 : -1;
-                const bool inz = lz + dz >= 0 && lz + dz < g.wz;
+                // a tile one cell thick along an axis always reads that axis' partner from the halo
+                const bool inz = TZ > 1 && lz + dz >= 0 && lz + dz < g.wz;
                 const int dx = dir_x(Ms, TT);
                 const bool inx = lx + dx >= 0 && lx + dx < g.wx;
                 constexpr int dy = O == 0 ? 1 : -1;        // the other type's y partner
-                const bool iny = ly + dy >= 0 && ly + dy < g.wy;
+                const bool iny = TY > 1 && ly + dy >= 0 && ly + dy < g.wy;
                 const unsigned char* rb = buf + TT * L::SRC_T;
                 const unsigned char* ro = buf + O * L::SRC_T;
                 // per neighbour: address of run slot -fq (so source q sits at q) and the slot stride
