@@ -71,13 +71,12 @@ def peaks():
 # key: (kernel, N, storage, tile, stage depth, target class)
 NCU_TRAFFIC = {
     ("stage", 39, "fp32", (40, 2, 2), 2, 0): {
-        "bytes_per_cell": (3.712430e9 + 1.561510e9) / 80 ** 3,
+        "bytes_per_cell": (3.752485e9 + 1.561912e9) / 80 ** 3,
         "source": "profiles/stage_p39_200.md: P39 80^3 capture of the even-class pass, scaled to the grid"},
     ("stage", 39, "fp32", (40, 2, 2), 2, 1): {
-        "bytes_per_cell": (3.695265e9 + 1.641104e9) / 80 ** 3,
+        "bytes_per_cell": (3.735229e9 + 1.641269e9) / 80 ** 3,
         "source": "profiles/stage_p39_200.md: P39 80^3 capture of the odd-class pass, scaled to the grid"},
 }
-
 
 def traffic_per_launch(kernel, N, storage, tile, depth, cls, cells):
     t = NCU_TRAFFIC.get((kernel, N, storage, tuple(tile), depth, cls))
