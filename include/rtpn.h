@@ -43,7 +43,7 @@ extern "C" {
 #define RTPN_ECUDA        -4   /* a CUDA call failed (message in rtpn_last_error)                 */
 #define RTPN_ETIMEOUT     -5   /* a bounded device wait ran out                                   */
 #define RTPN_ENONFINITE   -6   /* NaN or Inf found by a diagnostic                                */
-#define RTPN_EUNSUPPORTED -7   /* valid request this build does not implement                     */
+#define RTPN_EUNSUPPORTED -7   /* valid request the compiled library does not implement          */
 #define RTPN_ESTATE       -8   /* call out of order (e.g. rtpn_step before rtpn_set_media)        */
 
 /* ---- boundaries ---- */
@@ -259,14 +259,16 @@ int rtpn_batch_synchronize(rtpn_batch* b);
 const char* rtpn_batch_last_error(const rtpn_batch* b);
 
 /* ======================================================================== autotuner
- * Pick the CTA tile of the register-window kernel by timing candidate tiles (a multiple of 32
- * threads, at most 256) on the object's own data; the state is copied aside first and restored, so
- * the moments are unchanged (needs device memory for one copy of the state: RTPN_ENOMEM if absent).
+ * Pick the configuration of the active kernel by timing candidates on the object's own data: CTA
+ * tiles of the register-window kernel (a multiple of 32 threads, at most 256), or the compiled
+ * (tile, stage depth) variants of the staged kernel.  The state is copied aside first and restored,
+ * so the moments are unchanged (needs device memory for one copy of the state: RTPN_ENOMEM if absent).
  * The best tile is applied, written to tile[3] and its time to *ms (one even + odd pass pair for a
  * context, one rtpn_batch_step(b, 1) for a batch); either output may be NULL.  Results are cached
  * for the process per (orders, precision, boundary, grid, device) and, when the environment
  * variable RTPN_TUNE_CACHE names a file, kept there across processes.  Synchronises.
- * RTPN_ESTATE without media; RTPN_EUNSUPPORTED if the window kernel is not active.
+ * RTPN_ESTATE without media; RTPN_EUNSUPPORTED if neither the window nor the staged kernel is
+ * active (a batch always runs the window kernel).
  */
 int rtpn_autotune(rtpn_ctx* ctx, int reps, int tile[3], double* ms);
 int rtpn_batch_autotune(rtpn_batch* b, int reps, int tile[3], double* ms);

@@ -344,7 +344,7 @@ const char* rtpn_strerror(int code) {
         case RTPN_ECUDA: return "CUDA error";
         case RTPN_ETIMEOUT: return "bounded device wait expired";
         case RTPN_ENONFINITE: return "non-finite values in the state";
-        case RTPN_EUNSUPPORTED: return "not supported by this build";
+        case RTPN_EUNSUPPORTED: return "not compiled into this library";
         case RTPN_ESTATE: return "call out of order";
         default: return "unknown status";
     }
