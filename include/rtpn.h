@@ -128,7 +128,8 @@ int rtpn_set_stream(rtpn_ctx* ctx, void* stream);
 /* Select the step kernel (RTPN_KERNEL_*) and its CTA tile (tile_x * tile_y * tile_z threads, one
  * cell each; all 0 = default).  RTPN_KERNEL_WINDOW: the tile must hold a multiple of 32 threads, at
  * most 256 (RTPN_EINVAL); default 32 x 4 x 2.  RTPN_KERNEL_STAGE: the tile must be one compiled for
- * N (RTPN_EUNSUPPORTED otherwise).  RTPN_KERNEL_AUTO picks STAGE, then WINDOW, then GENERIC.
+ * N (RTPN_EUNSUPPORTED otherwise).  RTPN_KERNEL_AUTO picks STAGE (for N >= 15), then WINDOW, then
+ * GENERIC.
  * RTPN_EUNSUPPORTED if the kernel is not compiled for (N, precision, nx); the previous selection
  * then stays. */
 int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z);

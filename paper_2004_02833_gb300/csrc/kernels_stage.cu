@@ -117,8 +117,8 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
         if (err != cudaSuccess) return (int)err;
     }
     if (!ctx->stage_mem) {
-        // per target class A: the coupling constants of the source class by column, type and run
-        // slot ([N+1][2][N/2+1][CPAD], see stage_impl.cuh), then the column starts of both classes
+        // per target class A: the coupling constants of the source class by column, type and slot q
+        // ([N+1][2][N/2+1][CPAD], see stage_impl.cuh), then the column starts of both classes
         const int nl = N / 2 + 1;
         std::vector<int> col(2 * (N + 2));
         for (int P = 0; P < 2; ++P) {
@@ -138,7 +138,10 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
                 for (int t = 0; t < win::ntypes(M); ++t)
                     for (int j = 0; j < win::column_len(N, M, B); ++j) {
                         const int src = col[B * (N + 2) + M] + t * win::column_len(N, M, B) + j;
-                        float* d = &tab[A][(((size_t)M * 2 + t) * nl + j) * stg::CPAD];
+                        // slot = the source's q = (l - B) / 2 (l = first l of the column + 2 j); slots of
+                        // l < M stay zero, so a sweep may start at a slot boundary below the column
+                        const int q = win::first_l(M, B) / 2 + j;
+                        float* d = &tab[A][(((size_t)M * 2 + t) * nl + q) * stg::CPAD];
                         const float* k = &t10[(size_t)src * 10];
                         for (int r = 0; r < 6; ++r) d[r] = k[r];      // z, x to M-1, x to M+1
                         for (int r = 0; r < 4; ++r) d[8 + r] = k[6 + r];  // y to M-1, y to M+1

@@ -62,6 +62,14 @@ using win::static_for;
     default:                                                                                        \
         break;
 constexpr int kMaxSlots = 24;
+// The same for chunks of kChunk slots: `switch (first / kChunk) { RTPN_CHUNK_CASES(f) }` runs f(c) for
+// chunks c = first / kChunk .. 5, so a compiler sees kChunk slots as one straight-line block.
+constexpr int kChunk = 4;
+#define RTPN_CHUNK_CASES(f)                                                                        \
+    RTPN_SLOT_CASE(f, 0) RTPN_SLOT_CASE(f, 1) RTPN_SLOT_CASE(f, 2) RTPN_SLOT_CASE(f, 3)             \
+    RTPN_SLOT_CASE(f, 4) RTPN_SLOT_CASE(f, 5)                                                       \
+    default:                                                                                        \
+        break;
 
 constexpr unsigned STATUS_TIMEOUT = 1u;
 constexpr unsigned STATUS_CHECK = 2u;  // a self-check failed (builds with RTPN_STAGE_CHECKS)
@@ -74,7 +82,7 @@ constexpr int CPAD = 12;
 struct Args {
     void* u;
     const float* fac;
-    const float* coefcol;   // [column 0..N][type][run slot 0..N/2][CPAD] of the source class
+    const float* coefcol;   // [column 0..N][type][slot q 0..N/2][CPAD] of the source class (0 for l < M)
     const int* colstart;    // [2][N+2]: first local index of column M in class 0 / class 1
     long long V;
     int nx, ny, nz, bc;
@@ -141,11 +149,18 @@ struct Layout {
     static constexpr int HXO = R_CTR, HYO = R_CTR + R_HX, HZO = R_CTR + R_HX + R_HY;
     static constexpr int COEF_COL = 2 * NLC * CPAD * 4;     // one column's coupling constants
     static constexpr int R_TGT = pad128(NL * CTR_BYTES);     // tile boxes of one type's targets
-    static constexpr int TGTO = 2 * SRC_T;
-    static constexpr int COEFO = TGTO + 2 * R_TGT;
+    // buffer layout: target boxes, type-0 sources, type-1 sources, coupling constants.  A chunked
+    // sweep reads up to kChunk - 1 slots (plus one neighbour offset) below a source region; with the
+    // targets first, such reads stay on state data (or the zeros the ring starts with) in the same
+    // buffer, never on the coupling constants, whose bits need not be finite in the storage type.
+    static constexpr int TGTO = 0;
+    static constexpr int SRCO = 2 * R_TGT;
+    static constexpr int COEFO = SRCO + 2 * SRC_T;
     static constexpr int BUF = COEFO + pad128(COEF_COL);     // one stage buffer
     static constexpr int BARS = pad128(2 * NB * 8);
     static constexpr int BYTES = NB * BUF + BARS + 128;      // ring, mbarriers, base alignment slack
+    static_assert(2 * R_TGT >= (kChunk - 1) * CTR_BYTES + TX * TY * ES,
+                  "the target region must cover what a chunked sweep reads below the sources");
     static_assert(TX % HX == 0, "tile width must be a multiple of the 16-byte group");
     static_assert(CELLS % 32 == 0, "a type's threads must fill whole warps");
     static_assert(CTR_BYTES % 16 == 0 && HX_BYTES % 16 == 0 && HY_BYTES % 16 == 0 && HZ_BYTES % 16 == 0,
@@ -375,7 +390,7 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
             const int t = j / (4 * NG), kind = (j / NG) % 4, k = j % NG;
             if (t >= nt || k >= nbox) continue;
             const int c = cB0 + offB_s + t * len + k * E;  // first component of the box
-            const unsigned d = smem_addr(buf + t * L::SRC_T);
+            const unsigned d = smem_addr(buf + L::SRCO + t * L::SRC_T);
             if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 101, c)) continue;
             if (kind == 0) {
                 tma_load_4d(d + k * E * L::CTR_BYTES, maps, g.x0, g.y0, g.z0, c, full);
@@ -421,8 +436,13 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     // TMA writes into shared memory need 128-byte aligned destinations; the dynamic shared memory
     // window is not guaranteed to start on one, so the layout starts at the next 128-byte boundary.
     smem += (128u - (smem_addr(smem) & 127u)) & 127u;
+    // zero the ring once: slots a chunked sweep reads below a column's first source
+    // (with zero coupling constants) then always hold finite values
+    for (int k = tid; k < NB * L::BUF / 16; k += blockDim.x)
+        reinterpret_cast<uint4*>(smem)[k] = make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // before the TMA writes the ring
     unsigned char* bufs = smem;
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + NB * L::BUF);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(bufs + NB * L::BUF);
     const unsigned full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[NB]);
     if (tid == 0) {
         for (int b = 0; b < NB; ++b) {
@@ -520,8 +540,8 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                 const bool inx = lx + dx >= 0 && lx + dx < g.wx;
                 constexpr int dy = O == 0 ? 1 : -1;        // the other type's y partner
                 const bool iny = TY > 1 && ly + dy >= 0 && ly + dy < g.wy;
-                const unsigned char* rb = buf + TT * L::SRC_T;
-                const unsigned char* ro = buf + O * L::SRC_T;
+                const unsigned char* rb = buf + L::SRCO + TT * L::SRC_T;
+                const unsigned char* ro = buf + L::SRCO + O * L::SRC_T;
                 // per neighbour: address of run slot -fq (so source q sits at q) and the slot stride
                 const unsigned char* pc = rb + my - fq * L::CTR_BYTES;
                 const unsigned char* px =
@@ -536,8 +556,8 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                 const unsigned char* py =
                     iny ? po + dy * TX * L::ES : ro + L::HYO + (lz * TX + lx) * L::ES - fq * L::HY_BYTES;
                 const int sy = iny ? L::CTR_BYTES : L::HY_BYTES;
-                const float4* cown = reinterpret_cast<const float4*>(cf + (TT * L::NLC - fq) * CPAD);
-                const float4* coth = reinterpret_cast<const float4*>(cf + (O * L::NLC - fq) * CPAD);
+                const float4* cown = reinterpret_cast<const float4*>(cf + TT * L::NLC * CPAD);
+                const float4* coth = reinterpret_cast<const float4*>(cf + O * L::NLC * CPAD);
                 // sources q = fq .. NLB - 1 (q < fq has l < Ms: not in the column)
                 auto sweep = [&](auto own_c, auto oth_c) {
                     constexpr bool OWN = decltype(own_c)::value, OTH = decltype(oth_c)::value;
@@ -549,7 +569,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                             constexpr bool has_m = ls - 1 >= 0 && lm < NLA;
                             constexpr bool has_p = ls + 1 <= N && lp < NLA;
                             if constexpr (has_m || has_p) {
-                                if (!RTPN_SCHECK(q - fq >= 0 && q - fq < column_len(N, Ms, B))) return;
+                                if (!RTPN_SCHECK(q - fq >= -(kChunk - 1) && q - fq < column_len(N, Ms, B))) return;
                                 constexpr int am = has_m ? lm : 0, ap = has_p ? lp : 0;
                                 if constexpr (OWN) {
                                     const float c = lds<S>(pc, q * L::CTR_BYTES);
@@ -575,7 +595,15 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                             }
                         }
                     };
-                    switch (fq) { RTPN_SLOT_CASES(slot) }
+                    // chunks of kChunk slots from the one holding fq; slots below fq carry zero
+                    // coupling constants and read finite (zeroed or earlier) shared memory
+                    auto chunk = [&](auto ci) {
+                        constexpr int C = decltype(ci)::value;
+                        static_for<kChunk>([&](auto ki) {
+                            slot(std::integral_constant<int, C * kChunk + decltype(ki)::value>{});
+                        });
+                    };
+                    switch (fq / kChunk) { RTPN_CHUNK_CASES(chunk) }
                 };
                 // at |m| = 0 only the cos type exists
                 if (Ms == 0)
