@@ -314,6 +314,14 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / args.steps
+        # the dominant pass against the copy bandwidth on BF16's algorithmic bytes (2 B per moment)
+        info = c.info()
+        per_pass = pass_durations(c, stream, reps=5)
+        V = inst.shape[0] * inst.shape[1] * inst.shape[2]
+        alg = {cls: V * ((info.n_c + n_a) * 2 + 6) for cls, n_a in ((0, info.n_even), (1, info.n_odd))}
+        dom = max(per_pass, key=lambda k: per_pass[k])
+        hbm, _ = peaks()
+        pass_frac = alg[dom] / (per_pass[dom] / 1e3) / 1e9 / hbm
         c.close()
         # accuracy at the stated bounds on the 24^3 instance with the same rules (100 steps)
         small = synth.random_blocks(args.N, 24, seed=2)
@@ -329,6 +337,7 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
         bound = max(2e-2, 2.0 * (2 * 100 + 1) ** 0.5 * 2.0 ** -9)
         return {"ms_per_step": ms, "speedup_vs_fp32": fp32_ms / ms,
                 "value": mcu_step / (ms / 1e3) / 1e6, "unit": UNIT,
+                "pass_ms": per_pass, "pass_frac_of_copy_bw": pass_frac,
                 "max_rel_err_vs_fp64_100_steps_24cubed": err["bf16"], "bound": bound,
                 "fp32_max_rel_err_vs_fp64_100_steps_24cubed": err["fp32"], "fp32_bound": 1e-5}
 

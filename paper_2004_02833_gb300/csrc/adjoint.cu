@@ -404,8 +404,20 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
                                                                (const F*)dfac.p, tf[cls], g, ofs,
                                                                ctx->media + 2 * V, (double*)gacc.p,
                                                                (double*)gqb.p);
-            k_adj_sources<F><<<blocks_for(V, 128), 128, 0, st>>>((F*)lam.p, (const F*)wbuf.p, tt[1 - cls].tab,
-                                                            tf[cls].a0, g);
+            bool staged = false;
+            if constexpr (sizeof(F) == 4) {
+                // the transposed coupling on the staged kernel (same column sweep as a forward pass
+                // on class 1 - cls, sources w, lam += K w / h)
+                if (ctx->active_kernel == RTPN_KERNEL_STAGE) {
+                    const int rc2 = launch_stage_adjoint_sources(ctx, 1 - cls, (float*)lam.p, (const float*)wbuf.p,
+                                                                 std::max(ctx->md.ne, ctx->md.no), st);
+                    if (rc2) return afail(ctx, RTPN_ECUDA, "adjoint: staged transposed coupling failed");
+                    staged = true;
+                }
+            }
+            if (!staged)
+                k_adj_sources<F><<<blocks_for(V, 128), 128, 0, st>>>((F*)lam.p, (const F*)wbuf.p, tt[1 - cls].tab,
+                                                                tf[cls].a0, g);
         }
     }
     cudaMemcpyAsync(u, fin.p, state, cudaMemcpyDeviceToDevice, st);

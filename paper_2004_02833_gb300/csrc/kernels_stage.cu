@@ -12,7 +12,7 @@ namespace rtpn {
 namespace stg {
 
 #define RTPN_SDECL(n, x, y, z, b, e)                                                                 \
-    int stage_launch_##n##_##x##_##y##_##z##_##b##_##e(int, int, const Args&, int, cudaStream_t);       \
+    int stage_launch_##n##_##x##_##y##_##z##_##b##_##e(int, int, int, const Args&, int, cudaStream_t);  \
     int stage_smem_##n##_##x##_##y##_##z##_##b##_##e(int, int);                                          \
     int stage_boxcomps_##n##_##x##_##y##_##z##_##b##_##e(int);
 RTPN_STAGE_VARIANTS(RTPN_SDECL)
@@ -20,7 +20,7 @@ RTPN_STAGE_VARIANTS(RTPN_SDECL)
 
 struct Variant {
     int N, tx, ty, tz, depth;
-    int (*launch)(int, int, const Args&, int, cudaStream_t);
+    int (*launch)(int, int, int, const Args&, int, cudaStream_t);  // (cls, precision, mode, ...)
     int (*smem)(int, int);
     int (*boxcomps)(int);
 };
@@ -109,12 +109,14 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
         !stg::make_map(&maps[3], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, 1, e))
         return (int)cudaErrorInvalidValue;
     if (!ctx->stage_maps_dev) {
-        cudaError_t err = cudaMalloc(&ctx->stage_maps_dev, sizeof(maps));
+        // the forward's four maps, then room for the adjoint's five
+        cudaError_t err = cudaMalloc(&ctx->stage_maps_dev, 9 * sizeof(CUtensorMap));
         if (err != cudaSuccess) return (int)err;
     }
     {
         cudaError_t err = cudaMemcpy(ctx->stage_maps_dev, maps, sizeof(maps), cudaMemcpyHostToDevice);
         if (err != cudaSuccess) return (int)err;
+        ctx->stage_adj_lam = ctx->stage_adj_w = nullptr;  // the adjoint's maps follow the tile
     }
     if (!ctx->stage_mem) {
         // per target class A: the coupling constants of the source class by column, type and slot q
@@ -188,7 +190,7 @@ int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long
     if (ctx->stage_variant < 0) return (int)cudaErrorNotSupported;
     const stg::Variant& v = stg::kVariants[ctx->stage_variant];
     stg::Args a;
-    a.u = ctx->u;
+    a.tgt = ctx->u;
     a.fac = (const float*)ctx->fac;
     // class cls's targets read the coefficients of the other class's sources (table A = cls)
     const char* m = (const char*)ctx->stage_mem;
@@ -214,11 +216,69 @@ int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long
         a.kz = kz < 1 ? 1 : (kz > a.ntz ? a.ntz : kz);
     }
     a.maps = (const CUtensorMap*)ctx->stage_maps_dev;
+    a.tmap = a.maps;  // target boxes: the tile map over the same state
+    a.src_c0 = cls == 1 ? 0 : ctx->md.ne;  // the source class is the other one
     a.nc = ctx->md.nc;
     a.status = ctx->status;
     a.wait_limit = (unsigned)(wait_limit > 0xffffffffll ? 0xffffffffll : wait_limit);
     a.skip_stage = skip_stage;
-    return v.launch(cls, ctx->prec, a, ctx->sms, st);
+    return v.launch(cls, ctx->prec, stg::FORWARD, a, ctx->sms, st);
+}
+
+int launch_stage_adjoint_sources(rtpn_ctx* ctx, int tgt_cls, float* lam, const float* w, int w_planes,
+                                 cudaStream_t st) {
+    if (ctx->stage_variant < 0 || ctx->prec != RTPN_FP32) return (int)cudaErrorNotSupported;
+    const stg::Variant& v = stg::kVariants[ctx->stage_variant];
+    // tensor maps over w (the four source box kinds) and over lam (target tile boxes), rebuilt when
+    // the arrays change (once per adjoint call); they follow the forward maps at slots 4..8
+    CUtensorMap* dev = (CUtensorMap*)ctx->stage_maps_dev + 4;
+    if (ctx->stage_adj_lam != lam || ctx->stage_adj_w != w) {
+        const int e = v.boxcomps(RTPN_FP32);
+        alignas(64) CUtensorMap maps[5];
+        void* wp = const_cast<float*>(w);
+        if (!stg::make_map(&maps[0], wp, RTPN_FP32, ctx->g, w_planes, v.tx, v.ty, v.tz, e) ||
+            !stg::make_map(&maps[1], wp, RTPN_FP32, ctx->g, w_planes, 4, v.ty, v.tz, e) ||
+            !stg::make_map(&maps[2], wp, RTPN_FP32, ctx->g, w_planes, v.tx, 1, v.tz, e) ||
+            !stg::make_map(&maps[3], wp, RTPN_FP32, ctx->g, w_planes, v.tx, v.ty, 1, e) ||
+            !stg::make_map(&maps[4], lam, RTPN_FP32, ctx->g, ctx->md.nc, v.tx, v.ty, v.tz, e))
+            return (int)cudaErrorInvalidValue;
+        cudaError_t err = cudaMemcpy(dev, maps, sizeof(maps), cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) return (int)err;
+        ctx->stage_adj_lam = lam;
+        ctx->stage_adj_w = w;
+    }
+    stg::Args a;
+    a.tgt = lam;
+    a.fac = nullptr;
+    const char* m = (const char*)ctx->stage_mem;
+    // the coupling table of a forward pass on the target class: its sources are the other class
+    a.coefcol = (const float*)(tgt_cls == 0 ? m : m + ctx->stage_tab_bytes[0]);
+    a.colstart = (const int*)(m + ctx->stage_tab_bytes[0] + ctx->stage_tab_bytes[1]);
+    a.V = ctx->g.V;
+    a.nx = ctx->g.nx;
+    a.ny = ctx->g.ny;
+    a.nz = ctx->g.nz;
+    a.bc = ctx->g.bc;
+    a.fac_ofs = 0;
+    a.inv_h = (float)(1.0 / ctx->g.h);
+    a.ntx = (a.nx + v.tx - 1) / v.tx;
+    a.nty = (a.ny + v.ty - 1) / v.ty;
+    a.ntz = (a.nz + v.tz - 1) / v.tz;
+    a.tiles = (long long)a.ntx * a.nty * a.ntz;
+    if (a.tiles * (ctx->N + 2) >= (1ll << 31)) return (int)cudaErrorInvalidValue;
+    {
+        const double side = std::sqrt((double)(ctx->sms > 0 ? ctx->sms : 1) / a.ntx);
+        int kz = (int)(side + 0.5);
+        a.kz = kz < 1 ? 1 : (kz > a.ntz ? a.ntz : kz);
+    }
+    a.maps = dev;
+    a.tmap = dev + 4;
+    a.src_c0 = 0;  // w holds only the source class, in its local order
+    a.nc = w_planes;
+    a.status = ctx->status;
+    a.wait_limit = (unsigned)STAGE_WAIT_LIMIT;
+    a.skip_stage = -1;
+    return v.launch(tgt_cls, RTPN_FP32, stg::ADJ_SOURCES, a, ctx->sms, st);
 }
 
 }  // namespace rtpn

@@ -95,6 +95,11 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth);
 int stage_variants_of(int N, int precision, int* tiles, int max);
 int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long skip_stage,
                  long long wait_limit);
+// The transposed coupling of a substep for the adjoint's multipliers on the staged kernel:
+// lam_B += (1/h) K w_A (class B = tgt_cls; w: the w_planes planes of the other class, local order).
+// FP32 contexts with the staged kernel prepared; returns cudaError_t.
+int launch_stage_adjoint_sources(rtpn_ctx* ctx, int tgt_cls, float* lam, const float* w, int w_planes,
+                                 cudaStream_t st);
 constexpr long long STAGE_WAIT_LIMIT = 1ll << 20;  // mbarrier polls (each <= 2 us) before a wait gives up
 
 }  // namespace rtpn
@@ -126,5 +131,8 @@ struct rtpn_ctx {
     void* stage_mem = nullptr;       // staged kernels: coupling tables of both classes + column starts
     size_t stage_tab_bytes[2] = {0, 0};
     int stage_variant = -1, sms = 0;
-    void* stage_maps_dev = nullptr;  // four CUtensorMap of the staged kernel (device global memory)
+    void* stage_maps_dev = nullptr;  // CUtensorMap of the staged kernel (device global memory): 4 over u,
+                                     // then 5 for the adjoint (4 over its w, 1 over its lam)
+    const void* stage_adj_lam = nullptr;  // arrays the adjoint maps were built for
+    const void* stage_adj_w = nullptr;
 };

@@ -23,14 +23,14 @@ namespace {
 constexpr int kN = RTPN_SN, kTX = RTPN_STX, kTY = RTPN_STY, kTZ = RTPN_STZ, kNB = RTPN_SNB, kEM = RTPN_SEM;
 constexpr int kThreads = Layout<kN, 0, float, kTX, kTY, kTZ, kNB, kEM>::THREADS;
 
-template <int A, typename S>
+template <int A, typename S, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_stage(Args a) {
     static_assert(Layout<kN, A, S, kTX, kTY, kTZ, kNB, kEM>::FITS, "stage ring exceeds shared memory");
     extern __shared__ __align__(128) unsigned char smem[];
-    stage_kernel_body<kN, A, S, kTX, kTY, kTZ, kNB, kEM>(a, smem);
+    stage_kernel_body<kN, A, S, kTX, kTY, kTZ, kNB, kEM, MODE>(a, smem);
 }
 
-template <int A, typename S>
+template <int A, typename S, int MODE>
 int launch_one(const Args& a, int sms, cudaStream_t st) {
     using L = Layout<kN, A, S, kTX, kTY, kTZ, kNB, kEM>;
     if constexpr (!L::FITS) {
@@ -41,29 +41,35 @@ int launch_one(const Args& a, int sms, cudaStream_t st) {
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
     if (!configured[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_stage<A, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_stage<A, S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              L::BYTES);
         if (e != cudaSuccess) return (int)e;
         configured[dev] = true;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<A, S>, kThreads, L::BYTES);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<A, S, MODE>, kThreads, L::BYTES);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) return (int)cudaErrorLaunchOutOfResources;
     long long grid = (long long)per_sm * sms;
     if (grid > a.tiles) grid = a.tiles;
     if (grid < 1) return 0;
-    k_stage<A, S><<<(unsigned)grid, kThreads, L::BYTES, st>>>(a);
+    k_stage<A, S, MODE><<<(unsigned)grid, kThreads, L::BYTES, st>>>(a);
     return (int)cudaGetLastError();
     }
 }
 
 }  // namespace
 
-int RTPN_SVARIANT(stage_launch)(int cls, int precision, const Args& a, int sms, cudaStream_t st) {
+// mode FORWARD: FP32 or BF16 storage; mode ADJ_SOURCES: FP32 arrays (the adjoint's multipliers)
+int RTPN_SVARIANT(stage_launch)(int cls, int precision, int mode, const Args& a, int sms, cudaStream_t st) {
+    if (mode == ADJ_SOURCES) {
+        if (precision != RTPN_FP32) return (int)cudaErrorNotSupported;
+        return cls == 0 ? launch_one<0, float, ADJ_SOURCES>(a, sms, st) : launch_one<1, float, ADJ_SOURCES>(a, sms, st);
+    }
     if (precision == RTPN_BF16)
-        return cls == 0 ? launch_one<0, __nv_bfloat16>(a, sms, st) : launch_one<1, __nv_bfloat16>(a, sms, st);
-    return cls == 0 ? launch_one<0, float>(a, sms, st) : launch_one<1, float>(a, sms, st);
+        return cls == 0 ? launch_one<0, __nv_bfloat16, FORWARD>(a, sms, st)
+                        : launch_one<1, __nv_bfloat16, FORWARD>(a, sms, st);
+    return cls == 0 ? launch_one<0, float, FORWARD>(a, sms, st) : launch_one<1, float, FORWARD>(a, sms, st);
 }
 
 // dynamic shared memory of the variant, or 0 if it does not fit a CTA

@@ -80,8 +80,14 @@ constexpr unsigned STATUS_CHECK = 2u;  // a self-check failed (builds with RTPN_
 //   [8..11] y to column M-1 (l-1), (l+1), to M+1 (l-1), (l+1)  read by the thread of the other type
 constexpr int CPAD = 12;
 
+// What a pass computes.  FORWARD: targets u_A' = alpha u_A - beta acc (Eq. 5; the u_0 factors for
+// l = 0).  ADJ_SOURCES: the transpose of a substep's coupling for the dual multipliers,
+// lam_B' = lam_B + acc / h with the sources the weights w_A = beta_A lam_A of the substep on class A
+// (same stencil rule and coefficient table as a forward pass on class B: see csrc/adjoint.cu).
+constexpr int FORWARD = 0, ADJ_SOURCES = 1;
+
 struct Args {
-    void* u;
+    void* tgt;              // target array (u for a forward pass, lam for ADJ_SOURCES)
     const float* fac;
     const float* coefcol;   // [column 0..N][type][slot q 0..N/2][CPAD] of the source class (0 for l < M)
     const int* colstart;    // [2][N+2]: first local index of column M in class 0 / class 1
@@ -92,7 +98,9 @@ struct Args {
     int ntx, nty, ntz;
     int kz;                 // tile layers per z chunk of the walk
     long long tiles;
-    const CUtensorMap* maps;  // four tensor maps in global memory: tile, x halo, y halo, z halo
+    const CUtensorMap* maps;  // four tensor maps over the source array: tile, x halo, y halo, z halo
+    const CUtensorMap* tmap;  // tile map over the target array
+    int src_c0;               // first component of the source class in the source array
     int nc;                   // components (bound of the 4th tensor coordinate)
     unsigned* status;       // device status word (STATUS_TIMEOUT on a wait that ran out)
     unsigned wait_limit;    // try_wait polls (each up to WAIT_HINT_NS) before giving up
@@ -324,7 +332,7 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
     constexpr int E = L::E, NG = L::NG;
     const int lane = threadIdx.x & 31;
     const int cA0 = A == 0 ? 0 : class_size(N, 0);
-    const int cB0 = B == 0 ? 0 : class_size(N, 0);
+    const int cB0 = a.src_c0;
     const CUtensorMap* maps = a.maps;
     // first local index of source column i in class B and of target column i - 1 in class A,
     // advanced column by column (no table loads on the producer's path)
@@ -333,6 +341,7 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + k) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(a.tmap) : "memory");
 
     int s = 0;
     bool failed = false;
@@ -384,7 +393,7 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
                 if (t >= ntA || k >= nboxA) continue;
                 const int c = cA0 + offA_s + t * lenA + k * E;
                 if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 111, c)) continue;
-                tma_load_4d(smem_addr(buf + L::TGTO + t * L::R_TGT) + k * E * L::CTR_BYTES, maps, g.x0, g.y0,
+                tma_load_4d(smem_addr(buf + L::TGTO + t * L::R_TGT) + k * E * L::CTR_BYTES, a.tmap, g.x0, g.y0,
                             g.z0, c, full);
                 continue;
             }
@@ -417,7 +426,7 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
         if (r != a.skip_stage) wait_phase(full0 + 8 * (r % NB), (unsigned)((r / NB) & 1), a.wait_limit);
 }
 
-template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EM>
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EM, int MODE>
 __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* smem) {
     using L = Layout<N, A, S, TX, TY, TZ, NB, EM>;
     static_assert(N >= 1, "order N >= 1");
@@ -480,7 +489,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     // of the column finished next); component q = 0 of the run (type T, column M) at this cell
     int offA = 0;
     auto tgt_ptr = [&](int M) {
-        return reinterpret_cast<S*>(a.u) +
+        return reinterpret_cast<S*>(a.tgt) +
                (long long)(cA0 + offA + T * column_len(N, M, A) - first_l(M, A) / 2) * V + cell;
     };
 
@@ -493,7 +502,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
             g = tile_geo<TX, TY, TZ, HX>(a, tile);
             active = lx < g.wx && ly < g.wy && lz < g.wz;
             cell = ((long long)(g.z0 + lz) * a.ny + (g.y0 + ly)) * a.nx + (g.x0 + lx);
-            if (active) {
+            if (MODE == FORWARD && active) {
                 // sub-grid slot of (l, M, T) in class A: x by (M, T), y by T, z by (A + M)
 #pragma unroll
                 for (int par = 0; par < 2; ++par) {
@@ -627,7 +636,9 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                 if constexpr (q < NLA) {
                     const float old = lds<S>(ob, q * L::CTR_BYTES);
                     float nv;
-                    if (A == 0 && q == 0 && M == 0)
+                    if constexpr (MODE == ADJ_SOURCES)
+                        nv = fmaf(a.inv_h, prev[q], old);
+                    else if (A == 0 && q == 0 && M == 0)
                         nv = fmaf(al0, old, fmaf(-be0, prev[q], ga0));
                     else
                         nv = fmaf(alpha, old, -beta * prev[q]);

@@ -39,6 +39,26 @@ def test_adjoint_matches_oracle(cuda_device, coupling_cache, bc, precision, tol,
     assert rel(final, P.run(u0, 5)) <= max(tol, 1e-12)
 
 
+@pytest.mark.parametrize("bc", ["periodic", "vacuum"])
+def test_adjoint_staged_kernel_fp32_vs_oracle(cuda_device, coupling_cache, bc):
+    # FP32 with the staged kernel: the forward recomputation and the transposed coupling of every
+    # backward substep (lam_B += K w / h) run on it; full and partial tiles (nx = 40 > 32)
+    N, shape = 15, (4, 5, 40)
+    inst, u0 = synth.random_instance(N, shape, seed=43, bc=bc)
+    w = np.random.default_rng(44).uniform(0.0, 1.0, shape)
+    mats, slots = coupling_cache(N)
+    P = st.Problem(N, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, bc, mats=mats, slots=slots)
+    J_ref, gsa_ref, gss_ref, gq_ref = P.gradient(u0, 3, w)
+    with rtpn.Context(N, shape, inst.h, bc, "fp32", inst.dt) as ctx:
+        ctx.set_kernel("stage")
+        assert ctx.info().kernel == 3
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        J, (gsa, gss, gq) = ctx.adjoint(w, 3, ckpt_every=2)
+    assert abs(J - J_ref) <= 1e-4 * abs(J_ref)
+    assert rel(gsa, gsa_ref) <= 1e-4 and rel(gss, gss_ref) <= 1e-4 and rel(gq, gq_ref) <= 1e-4
+
+
 def test_adjoint_p3_32_checkerboard_fp64(cuda_device, coupling_cache):
     # P3 on 32^3 in FP64: the lattice scaled to 32^3, vacuum, zero start, detector box scaled
     inst = synth.checkerboard(3, 32)
