@@ -389,6 +389,17 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
     Buf fin;
     if (!fin.alloc(state)) return afail(ctx, RTPN_ENOMEM, "adjoint: final state");
     cudaMemcpyAsync(fin.p, u, state, cudaMemcpyDeviceToDevice, st);
+    // FP32 with the staged kernel: tensor maps over every pre-substep state slot of a segment
+    Buf premaps;
+    bool staged_targets = false;
+    if constexpr (sizeof(F) == 4 && sizeof(S) == 4) {
+        if (ctx->active_kernel == RTPN_KERNEL_STAGE) {
+            if (!premaps.alloc((size_t)npass * 4 * 128)) return afail(ctx, RTPN_ENOMEM, "adjoint: tensor maps");
+            staged_targets = true;
+            for (int p = 0; p < npass && staged_targets; ++p)
+                staged_targets = stage_maps_for(ctx, (char*)seg.p + (size_t)p * state, (char*)premaps.p + (size_t)p * 512) == 0;
+        }
+    }
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int s0 = sg * ckpt, s1 = std::min(k, s0 + ckpt);
         cudaMemcpyAsync(u, (char*)ck.p + (size_t)sg * state, state, cudaMemcpyDeviceToDevice, st);
@@ -400,10 +411,18 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
             const int cls = (p % 3 == 1) ? 0 : 1;
             const int ofs = (p % 3 == 1) ? FAC_FULL : FAC_HALF;
             const S* pre = (const S*)((char*)seg.p + (size_t)p * state);
-            k_adj_targets<S, F><<<blocks_for(V, 128), 128, 0, st>>>(pre, (F*)lam.p, (F*)wbuf.p, (const F*)ctx->fac,
-                                                               (const F*)dfac.p, tf[cls], g, ofs,
-                                                               ctx->media + 2 * V, (double*)gacc.p,
-                                                               (double*)gqb.p);
+            if (staged_targets) {
+                // the same pull-back on the staged kernel (column sweep over the pre-substep state)
+                const int rc2 = launch_stage_adjoint_targets(ctx, cls, ofs, (const char*)premaps.p + (size_t)p * 512,
+                                                             (float*)lam.p, (float*)wbuf.p, (const float*)dfac.p,
+                                                             ctx->media + 2 * V, (double*)gacc.p, (double*)gqb.p, st);
+                if (rc2) return afail(ctx, RTPN_ECUDA, "adjoint: staged pull-back failed");
+            } else {
+                k_adj_targets<S, F><<<blocks_for(V, 128), 128, 0, st>>>(pre, (F*)lam.p, (F*)wbuf.p, (const F*)ctx->fac,
+                                                                   (const F*)dfac.p, tf[cls], g, ofs,
+                                                                   ctx->media + 2 * V, (double*)gacc.p,
+                                                                   (double*)gqb.p);
+            }
             bool staged = false;
             if constexpr (sizeof(F) == 4) {
                 // the transposed coupling on the staged kernel (same column sweep as a forward pass

@@ -225,6 +225,65 @@ int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long
     return v.launch(cls, ctx->prec, stg::FORWARD, a, ctx->sms, st);
 }
 
+int stage_maps_for(rtpn_ctx* ctx, const void* state, void* maps_dev) {
+    if (ctx->stage_variant < 0 || ctx->prec != RTPN_FP32) return (int)cudaErrorNotSupported;
+    const stg::Variant& v = stg::kVariants[ctx->stage_variant];
+    const int e = v.boxcomps(RTPN_FP32);
+    alignas(64) CUtensorMap maps[4];
+    void* b = const_cast<void*>(state);
+    const int nc = ctx->md.nc;
+    if (!stg::make_map(&maps[0], b, RTPN_FP32, ctx->g, nc, v.tx, v.ty, v.tz, e) ||
+        !stg::make_map(&maps[1], b, RTPN_FP32, ctx->g, nc, 4, v.ty, v.tz, e) ||
+        !stg::make_map(&maps[2], b, RTPN_FP32, ctx->g, nc, v.tx, 1, v.tz, e) ||
+        !stg::make_map(&maps[3], b, RTPN_FP32, ctx->g, nc, v.tx, v.ty, 1, e))
+        return (int)cudaErrorInvalidValue;
+    return (int)cudaMemcpy(maps_dev, maps, sizeof(maps), cudaMemcpyHostToDevice);
+}
+
+int launch_stage_adjoint_targets(rtpn_ctx* ctx, int cls, int fac_ofs, const void* maps_dev, float* lam,
+                                 float* wout, const float* dfac, const double* qsrc, double* gacc, double* gq,
+                                 cudaStream_t st) {
+    if (ctx->stage_variant < 0 || ctx->prec != RTPN_FP32) return (int)cudaErrorNotSupported;
+    const stg::Variant& v = stg::kVariants[ctx->stage_variant];
+    stg::Args a{};
+    a.tgt = nullptr;  // nothing of the state is written
+    a.lam = lam;
+    a.wout = wout;
+    a.dfac = dfac;
+    a.qsrc = qsrc;
+    a.gacc = gacc;
+    a.gq = gq;
+    a.fac = (const float*)ctx->fac;
+    const char* m = (const char*)ctx->stage_mem;
+    a.coefcol = (const float*)(cls == 0 ? m : m + ctx->stage_tab_bytes[0]);
+    a.colstart = (const int*)(m + ctx->stage_tab_bytes[0] + ctx->stage_tab_bytes[1]);
+    a.V = ctx->g.V;
+    a.nx = ctx->g.nx;
+    a.ny = ctx->g.ny;
+    a.nz = ctx->g.nz;
+    a.bc = ctx->g.bc;
+    a.fac_ofs = fac_ofs;
+    a.inv_h = (float)(1.0 / ctx->g.h);
+    a.ntx = (a.nx + v.tx - 1) / v.tx;
+    a.nty = (a.ny + v.ty - 1) / v.ty;
+    a.ntz = (a.nz + v.tz - 1) / v.tz;
+    a.tiles = (long long)a.ntx * a.nty * a.ntz;
+    if (a.tiles * (ctx->N + 2) >= (1ll << 31)) return (int)cudaErrorInvalidValue;
+    {
+        const double side = std::sqrt((double)(ctx->sms > 0 ? ctx->sms : 1) / a.ntx);
+        int kz = (int)(side + 0.5);
+        a.kz = kz < 1 ? 1 : (kz > a.ntz ? a.ntz : kz);
+    }
+    a.maps = (const CUtensorMap*)maps_dev;
+    a.tmap = a.maps;  // the old target values come from the same pre-substep state
+    a.src_c0 = cls == 1 ? 0 : ctx->md.ne;
+    a.nc = ctx->md.nc;
+    a.status = ctx->status;
+    a.wait_limit = (unsigned)STAGE_WAIT_LIMIT;
+    a.skip_stage = -1;
+    return v.launch(cls, RTPN_FP32, stg::ADJ_TARGETS, a, ctx->sms, st);
+}
+
 int launch_stage_adjoint_sources(rtpn_ctx* ctx, int tgt_cls, float* lam, const float* w, int w_planes,
                                  cudaStream_t st) {
     if (ctx->stage_variant < 0 || ctx->prec != RTPN_FP32) return (int)cudaErrorNotSupported;

@@ -100,6 +100,14 @@ int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long
 // FP32 contexts with the staged kernel prepared; returns cudaError_t.
 int launch_stage_adjoint_sources(rtpn_ctx* ctx, int tgt_cls, float* lam, const float* w, int w_planes,
                                  cudaStream_t st);
+// Four tensor maps of the staged kernel over another FP32 state (an adjoint segment's pre-substep
+// state) into maps_dev (device, 4 CUtensorMap); returns cudaError_t.
+int stage_maps_for(rtpn_ctx* ctx, const void* state, void* maps_dev);
+// The pull-back of the multipliers through a substep on class cls from its pre-substep state (maps
+// from stage_maps_for): media gradients into gacc / gq, w of class cls, lam of class cls scaled.
+int launch_stage_adjoint_targets(rtpn_ctx* ctx, int cls, int fac_ofs, const void* maps_dev, float* lam,
+                                 float* wout, const float* dfac, const double* qsrc, double* gacc, double* gq,
+                                 cudaStream_t st);
 constexpr long long STAGE_WAIT_LIMIT = 1ll << 20;  // mbarrier polls (each <= 2 us) before a wait gives up
 
 }  // namespace rtpn

@@ -84,10 +84,21 @@ constexpr int CPAD = 12;
 // l = 0).  ADJ_SOURCES: the transpose of a substep's coupling for the dual multipliers,
 // lam_B' = lam_B + acc / h with the sources the weights w_A = beta_A lam_A of the substep on class A
 // (same stencil rule and coefficient table as a forward pass on class B: see csrc/adjoint.cu).
-constexpr int FORWARD = 0, ADJ_SOURCES = 1;
+// ADJ_TARGETS: the pull-back through a substep on class A of the adjoint's multipliers: from the
+// pre-substep state, the forward residual r_A = -acc / h (+ q for u_0), the media gradients
+// gacc[slot] += lam_A (dalpha u_A + dbeta r_A) (and gq += beta_0 lam_0), w_A = beta_A lam_A and
+// lam_A <- alpha_A lam_A.
+constexpr int FORWARD = 0, ADJ_SOURCES = 1, ADJ_TARGETS = 2;
 
 struct Args {
     void* tgt;              // target array (u for a forward pass, lam for ADJ_SOURCES)
+    // ADJ_TARGETS only
+    float* lam;             // multipliers [nc][V] (internal order), read and scaled in place
+    float* wout;            // w of the target class [local index][V]
+    const float* dfac;      // dalpha/dc, dbeta/dc planes (same slot layout as the factors; u_0: 32, 33)
+    const double* qsrc;     // q per cell (the u_0 source)
+    double* gacc;           // [9][V] media-gradient accumulators (slot codes 0..7, u_0)
+    double* gq;             // [V] source gradient
     const float* fac;
     const float* coefcol;   // [column 0..N][type][slot q 0..N/2][CPAD] of the source class (0 for l < M)
     const int* colstart;    // [2][N+2]: first local index of column M in class 0 / class 1
@@ -484,6 +495,11 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     long long cell = 0;
     float alE = 0.f, beE = 0.f, alO = 0.f, beO = 0.f;  // Eq. (5) factors of columns M even / odd
     float al0 = 0.f, be0 = 0.f, ga0 = 0.f;             // u_0 (class 0, type 0 only)
+    // ADJ_TARGETS: factor derivatives, the u_0 source, the multipliers of the target column being
+    // finished (prefetched at the top of the stage) and this tile's media-gradient sums
+    float daE = 0.f, dbE = 0.f, daO = 0.f, dbO = 0.f, da0 = 0.f, db0 = 0.f, q0s = 0.f;
+    float lpre[MODE == ADJ_TARGETS ? NLA : 1];
+    float gE = 0.f, gO = 0.f, g0 = 0.f, gqa = 0.f;
 
     // first local index of target column M in class A, advanced column by column (offA = colstart
     // of the column finished next); component q = 0 of the run (type T, column M) at this cell
@@ -502,7 +518,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
             g = tile_geo<TX, TY, TZ, HX>(a, tile);
             active = lx < g.wx && ly < g.wy && lz < g.wz;
             cell = ((long long)(g.z0 + lz) * a.ny + (g.y0 + ly)) * a.nx + (g.x0 + lx);
-            if (MODE == FORWARD && active) {
+            if (MODE != ADJ_SOURCES && active) {  // the transposed coupling uses no factors
                 // sub-grid slot of (l, M, T) in class A: x by (M, T), y by T, z by (A + M)
 #pragma unroll
                 for (int par = 0; par < 2; ++par) {
@@ -510,7 +526,9 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                     const int gz = ((A + par) & 1) == 0 ? 0 : 1;
                     const int gc = gx + 2 * T + 4 * gz;
                     const float al = __ldg(a.fac + (long long)(a.fac_ofs + 2 * gc) * V + cell);
-                    const float be = __ldg(a.fac + (long long)(a.fac_ofs + 2 * gc + 1) * V + cell) * a.inv_h;
+                    // the forward folds 1/h into beta; the adjoint keeps beta and da, db per slot
+                    const float be = __ldg(a.fac + (long long)(a.fac_ofs + 2 * gc + 1) * V + cell) *
+                                     (MODE == ADJ_TARGETS ? 1.f : a.inv_h);
                     if (par == 0) {
                         alE = al;
                         beE = be;
@@ -518,15 +536,40 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                         alO = al;
                         beO = be;
                     }
+                    if constexpr (MODE == ADJ_TARGETS) {
+                        const float da = __ldg(a.dfac + (long long)(a.fac_ofs + 2 * gc) * V + cell);
+                        const float db = __ldg(a.dfac + (long long)(a.fac_ofs + 2 * gc + 1) * V + cell);
+                        if (par == 0) {
+                            daE = da;
+                            dbE = db;
+                        } else {
+                            daO = da;
+                            dbO = db;
+                        }
+                    }
                 }
                 if (A == 0 && T == 0) {
                     al0 = __ldg(a.fac + (long long)FAC_U0 * V + cell);
-                    be0 = __ldg(a.fac + (long long)(FAC_U0 + 1) * V + cell) * a.inv_h;
+                    be0 = __ldg(a.fac + (long long)(FAC_U0 + 1) * V + cell) * (MODE == ADJ_TARGETS ? 1.f : a.inv_h);
                     ga0 = __ldg(a.fac + (long long)(FAC_U0 + 2) * V + cell);
+                    if constexpr (MODE == ADJ_TARGETS) {
+                        da0 = __ldg(a.dfac + 32ll * V + cell);
+                        db0 = __ldg(a.dfac + 33ll * V + cell);
+                        q0s = (float)a.qsrc[cell];
+                    }
                 }
             }
         }
         const bool fin = active && i >= 1 && (T == 0 || i - 1 >= 1);  // target column i - 1 of type T
+        if constexpr (MODE == ADJ_TARGETS) {
+            if (fin) {  // the multipliers of column i - 1, for the finish below
+                const int M = i - 1, q0 = first_l(M, A) / 2;
+                const float* lp = a.lam + (long long)(cA0 + offA + T * column_len(N, M, A) - q0) * V + cell;
+#pragma unroll
+                for (int q = 0; q < NLA; ++q)
+                    if (q >= q0) lpre[q] = __ldg(lp + (long long)q * V);
+            }
+        }
 
         if (!__all_sync(0xffffffffu, wait_phase(full0 + 8 * b, ph, a.wait_limit))) {
             if (lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
@@ -635,14 +678,38 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                 constexpr int q = decltype(qi)::value;
                 if constexpr (q < NLA) {
                     const float old = lds<S>(ob, q * L::CTR_BYTES);
-                    float nv;
-                    if constexpr (MODE == ADJ_SOURCES)
-                        nv = fmaf(a.inv_h, prev[q], old);
-                    else if (A == 0 && q == 0 && M == 0)
-                        nv = fmaf(al0, old, fmaf(-be0, prev[q], ga0));
-                    else
-                        nv = fmaf(alpha, old, -beta * prev[q]);
-                    win::store<S>(tp + (long long)q * V, nv);
+                    if constexpr (MODE == ADJ_TARGETS) {
+                        const float la = lpre[q];
+                        const float r = -a.inv_h * prev[q];  // the forward residual (without q)
+                        const long long loc = (long long)(offA + T * column_len(N, M, A) - q0 + q) * V + cell;
+                        float al, be;
+                        if (A == 0 && q == 0 && M == 0) {
+                            g0 = fmaf(la, fmaf(da0, old, db0 * (r + q0s)), g0);
+                            gqa = fmaf(be0, la, gqa);
+                            al = al0;
+                            be = be0;
+                        } else {
+                            const float da = (M & 1) ? daO : daE, db = (M & 1) ? dbO : dbE;
+                            const float gv = la * fmaf(da, old, db * r);
+                            if (M & 1)
+                                gO += gv;
+                            else
+                                gE += gv;
+                            al = alpha;
+                            be = beta;
+                        }
+                        a.wout[loc] = be * la;
+                        a.lam[(long long)cA0 * V + loc] = al * la;
+                    } else {
+                        float nv;
+                        if constexpr (MODE == ADJ_SOURCES)
+                            nv = fmaf(a.inv_h, prev[q], old);
+                        else if (A == 0 && q == 0 && M == 0)
+                            nv = fmaf(al0, old, fmaf(-be0, prev[q], ga0));
+                        else
+                            nv = fmaf(alpha, old, -beta * prev[q]);
+                        win::store<S>(tp + (long long)q * V, nv);
+                    }
                 }
             };
             switch (q0) { RTPN_SLOT_CASES(tslot) }
@@ -662,6 +729,22 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
             next[q] = 0.f;
         }
         if (i >= 1) offA += ntypes(i - 1) * column_len(N, i - 1, A);
+        if constexpr (MODE == ADJ_TARGETS) {
+            if (i == NST - 1 && active) {
+                // this tile's media-gradient sums: each (cell, slot code) belongs to one thread
+#pragma unroll
+                for (int par = 0; par < 2; ++par) {
+                    const int gx = ((par == 0) == (T == 0)) ? 0 : 1;
+                    const int gz = ((A + par) & 1) == 0 ? 0 : 1;
+                    a.gacc[(long long)(gx + 2 * T + 4 * gz) * V + cell] += (double)(par == 0 ? gE : gO);
+                }
+                if (A == 0 && T == 0) {
+                    a.gacc[8ll * V + cell] += (double)g0;
+                    a.gq[cell] += (double)gqa;
+                }
+                gE = gO = g0 = gqa = 0.f;
+            }
+        }
         if (i == NST - 1) {  // tile done: reset the window and the column offset
 #pragma unroll
             for (int q = 0; q < NLA; ++q) prev[q] = cur[q] = 0.f;
