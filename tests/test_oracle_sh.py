@@ -2,6 +2,8 @@
 mathematics fix (not against the oracle's own formulas)."""
 import math
 
+import os
+
 import numpy as np
 import pytest
 
@@ -133,7 +135,14 @@ def test_placement(coupling_cache, N):
     assert np.array_equal(sh.parity_class(slots), ls % 2)
 
 
-@pytest.mark.parametrize("N,printed", [(3, 68.3), (7, 50.5), (39, 45.1)])
+def _printed_flop_model():
+    """(N, FLOP per LCUP) as printed in Section 4.1.1 (tests/golden/flop_model.txt)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "flop_model.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return [(int(n), float(v)) for n, v in rows]
+
+
+@pytest.mark.parametrize("N,printed", _printed_flop_model())
 def test_flop_model_class_sizes(coupling_cache, N, printed):
     # Section 4.1.1 prints 392 + 40 v_e + 50 v_o FLOP per cell and 68.3 / 50.5 / 45.1 FLOP/LCUP.  The
     # printed values come out only with 40 per odd-grid and 50 per even-grid component (reading:
