@@ -71,10 +71,10 @@ def peaks():
 # key: (kernel, N, storage, tile, stage depth, target class)
 NCU_TRAFFIC = {
     ("stage", 39, "fp32", (40, 2, 2), 2, 0): {
-        "bytes_per_cell": (3.753060e9 + 1.562129e9) / 80 ** 3,
+        "bytes_per_cell": (3.752663e9 + 1.562384e9) / 80 ** 3,
         "source": "profiles/stage_p39_200.md: P39 80^3 capture of the even-class pass, scaled to the grid"},
     ("stage", 39, "fp32", (40, 2, 2), 2, 1): {
-        "bytes_per_cell": (3.735424e9 + 1.641428e9) / 80 ** 3,
+        "bytes_per_cell": (3.736720e9 + 1.642148e9) / 80 ** 3,
         "source": "profiles/stage_p39_200.md: P39 80^3 capture of the odd-class pass, scaled to the grid"},
 }
 
