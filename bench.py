@@ -40,7 +40,7 @@ def parse():
     p.add_argument("--N", type=int, default=39)
     p.add_argument("--n", type=int, default=200)
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
-    p.add_argument("--kernel", default="auto", choices=["auto", "generic", "window", "stage"])
+    p.add_argument("--kernel", default="auto", choices=["auto", "generic", "window", "stage", "fused"])
     p.add_argument("--tile", default="0,0,0")
     p.add_argument("--depth", type=int, default=0, help="stage buffers of the staged kernel (0 = default)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -242,7 +242,7 @@ def main():
     dom = max(per_pass, key=lambda c: per_pass[c])
     hbm, peak_kind = peaks()
     achieved = alg[dom] / (per_pass[dom] / 1e3) / 1e9
-    kname = {1: "generic", 2: "window", 3: "stage"}.get(ctx.info().kernel, "?")
+    kname = {1: "generic", 2: "window", 3: "stage", 4: "fused"}.get(ctx.info().kernel, "?")
     traffic, traffic_src = traffic_per_launch(kname, args.N, args.precision, tuple(ctx.info().tile),
                                               ctx.info().depth, dom, V)
     step_ms = ms / args.steps
@@ -275,7 +275,7 @@ def main():
             "data": "synthetic", "config": workload_config(args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": 2 * args.steps + 1, "nonfinite": nonfinite, "forms": forms,
-            "kernel_used": {1: "generic", 2: "window", 3: "stage"}.get(ctx.info().kernel, "?"),
+            "kernel_used": kname,
             "tile": list(ctx.info().tile), "depth": ctx.info().depth}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -391,7 +391,45 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
                 "speedup_vs_central_fd": (2 * 3 * V * t_fwd) / t_adj,
                 "note": "central differences of 3 per-cell fields need 2*3*V forward runs"}
 
+    def fused():
+        # the even full step and the odd step of each step in one pass between two state buffers,
+        # against the window kernel's two in-place passes, at P7 128^3 (the fused kernel's ring
+        # of new even planes fits shared memory up to N = 9)
+        inst = synth.random_blocks(7, 128, seed=5)
+        V = inst.shape[0] * inst.shape[1] * inst.shape[2]
+        k = 200
+        res = {}
+        for kern in ("window", "fused"):
+            c = rtpn.Context(7, inst.shape, inst.h, inst.bc, "fp32", inst.dt)
+            c.set_stream(stream)
+            c.set_kernel(kern)
+            c.set_media(*[torch.tensor(a, dtype=torch.float32, device="cuda")
+                          for a in (inst.sigma_a, inst.sigma_s, inst.q)])
+            c.zero_moments()
+            c.set_component(0, torch.tensor(inst.u0, dtype=torch.float32, device="cuda"))
+            c.step(3)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c.step(k)
+            e.record(stream)
+            torch.cuda.synchronize()
+            res[kern] = a.elapsed_time(e) / k
+            res[kern + "_u0_sum"] = c.sum_u0()
+            c.close()
+        hbm, _ = peaks()
+        # per step: every moment read once and written once, plus 12 B of media factors per cell
+        step_bytes = V * (64 * 2 * 4 + 12)
+        return {"workload": "P7 128^3 random-block media, periodic, FP32, 200 steps",
+                "window_ms_per_step": res["window"], "fused_ms_per_step": res["fused"],
+                "speedup_vs_window": res["window"] / res["fused"],
+                "fused_step_frac_of_copy_bw": step_bytes / (res["fused"] / 1e3) / 1e9 / hbm,
+                "window_step_frac_of_copy_bw": step_bytes / (res["window"] / 1e3) / 1e9 / hbm,
+                "u0_sum_rel_diff": abs(res["fused_u0_sum"] - res["window_u0_sum"]) /
+                                   max(abs(res["window_u0_sum"]), 1e-300),
+                "value": 64 * V / (res["fused"] / 1e3) / 1e6, "unit": UNIT}
+
     out["bf16"] = _guard(bf16)
+    out["fused"] = _guard(fused)
     out["batched"] = _guard(batched)
     out["adjoint"] = _guard(adjoint)
     return out

@@ -69,6 +69,9 @@ extern "C" {
 #define RTPN_KERNEL_WINDOW  2  /* FP32/BF16, compiled N: register-window scatter over m-columns  */
 #define RTPN_KERNEL_STAGE   3  /* FP32/BF16, compiled N, nx*elem a multiple of 16 B: column loop
                                   with TMA-staged shared-memory tiles, persistent CTAs          */
+#define RTPN_KERNEL_FUSED   4  /* FP32/BF16, compiled N (1, 3, 5, 7, 9): each (even full step, odd
+                                  step) pair of rtpn_step in one z-streaming pass between two
+                                  state buffers; single substeps use the window kernel          */
 
 typedef struct rtpn_ctx rtpn_ctx;
 
@@ -128,8 +131,10 @@ int rtpn_set_stream(rtpn_ctx* ctx, void* stream);
 /* Select the step kernel (RTPN_KERNEL_*) and its CTA tile (tile_x * tile_y * tile_z threads, one
  * cell each; all 0 = default).  RTPN_KERNEL_WINDOW: the tile must hold a multiple of 32 threads, at
  * most 256 (RTPN_EINVAL); default 32 x 4 x 2.  RTPN_KERNEL_STAGE: the tile must be one compiled for
- * N (RTPN_EUNSUPPORTED otherwise).  RTPN_KERNEL_AUTO picks STAGE (for N >= 15), then WINDOW, then
- * GENERIC.
+ * N (RTPN_EUNSUPPORTED otherwise).  RTPN_KERNEL_FUSED: the CTA tile is fixed at 32 x 8 cells, so
+ * tile_x and tile_y must be 0 (or 32 and 8); tile_z is the number of z planes a CTA streams through
+ * (0 = about two waves of CTAs).  Selecting it allocates a second state buffer (RTPN_ENOMEM if that
+ * fails).  RTPN_KERNEL_AUTO picks STAGE (for N >= 15), then WINDOW, then GENERIC.
  * RTPN_EUNSUPPORTED if the kernel is not compiled for (N, precision, nx); the previous selection
  * then stays. */
 int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z);
@@ -167,6 +172,11 @@ int rtpn_zero_moments(rtpn_ctx* ctx);
  * (even full step, odd full step) -- two adjacent odd half steps merged, exact because the even
  * class is frozen between them (Eq. 5) -- then an even full step and an odd half step.
  * Asynchronous on the context stream; the launch sequence is replayed from a cached CUDA graph.
+ * With RTPN_KERNEL_FUSED each (even full step, odd step) pair, the last one with the odd half step,
+ * is one pass from one state buffer into the other (the context keeps track of which holds the
+ * state; get/set/sum see the current one).  When the context stream is being captured by the
+ * caller, rtpn_step runs the two-pass schedule in place instead, so the captured pointers stay
+ * valid on replay.
  * RTPN_ESTATE if media were never set.
  */
 int rtpn_step(rtpn_ctx* ctx, int k);

@@ -33,11 +33,18 @@ def _nvcc() -> str:
 
 VARIANT_SRC = "window.cu"  # compiled once per (order, class) listed in window_variants.h
 STAGE_SRC = "stage.cu"     # compiled once per (order, tile, depth, box size) listed in stage_variants.h
+FUSED_SRC = "fused.cu"     # compiled once per order listed in fused_variants.h
 
 
 def window_orders() -> list[int]:
     text = open(os.path.join(CSRC, "window_variants.h")).read()
     line = [l for l in text.splitlines() if l.startswith("#define RTPN_WINDOW_ORDERS")][0]
+    return [int(v) for v in re.findall(r"X\((\d+)\)", line)]
+
+
+def fused_orders() -> list[int]:
+    text = open(os.path.join(CSRC, "fused_variants.h")).read()
+    line = [l for l in text.splitlines() if l.startswith("#define RTPN_FUSED_ORDERS")][0]
     return [int(v) for v in re.findall(r"X\((\d+)\)", line)]
 
 
@@ -52,13 +59,15 @@ def units() -> list[tuple[str, list[str], str]]:
     """(source, defines, object name) of every translation unit."""
     out = []
     for f in sorted(os.listdir(CSRC)):
-        if not f.endswith((".cu", ".cpp")) or f in (VARIANT_SRC, STAGE_SRC):
+        if not f.endswith((".cu", ".cpp")) or f in (VARIANT_SRC, STAGE_SRC, FUSED_SRC):
             continue
         out.append((os.path.join(CSRC, f), [], f + ".o"))
     for n in window_orders():
         for cls in (0, 1):
             out.append((os.path.join(CSRC, VARIANT_SRC), [f"-DRTPN_WN={n}", f"-DRTPN_WCLS={cls}"],
                         f"window_N{n}_c{cls}.o"))
+    for n in fused_orders():
+        out.append((os.path.join(CSRC, FUSED_SRC), [f"-DRTPN_FN={n}"], f"fused_N{n}.o"))
     for n, tx, ty, tz, nb, em in stage_variants():
         out.append((os.path.join(CSRC, STAGE_SRC),
                     [f"-DRTPN_SN={n}", f"-DRTPN_STX={tx}", f"-DRTPN_STY={ty}", f"-DRTPN_STZ={tz}",
@@ -88,7 +97,7 @@ def build(verbose: bool = False, extra: list[str] | None = None, jobs: int | Non
     todo = units()
     # longest units first so the parallel build ends sooner
     todo.sort(key=lambda u: -max([int(d.split("=")[1]) for d in u[1]
-                                  if d.startswith(("-DRTPN_WN", "-DRTPN_SN"))] or [0]))
+                                  if d.startswith(("-DRTPN_WN", "-DRTPN_SN", "-DRTPN_FN"))] or [0]))
     jobs = jobs or min(len(todo), max(2, os.cpu_count() or 2))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(lambda u: _compile(u, extra), todo))

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <stdexcept>
 #include <string>
+#include <utility>
 
 #include "rtpn_internal.h"
 
@@ -130,16 +131,17 @@ int run_pass(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st) {
         int rc = launch_stage(ctx, cls, fac_ofs, st, -1, STAGE_WAIT_LIMIT);
         if (rc) return fail(ctx, RTPN_ECUDA, std::string("staged kernel: ") +
                                                  cudaGetErrorString((cudaError_t)rc));
-    } else if (ctx->active_kernel == RTPN_KERNEL_WINDOW) {
+    } else if (ctx->active_kernel == RTPN_KERNEL_WINDOW || ctx->active_kernel == RTPN_KERNEL_FUSED) {
         WindowLaunch w;
         w.u = ctx->u;
         w.fac = (const float*)ctx->fac;
         w.g = ctx->g;
         w.cls = cls;
         w.fac_ofs = fac_ofs;
-        w.tx = ctx->tx;
-        w.ty = ctx->ty;
-        w.tz = ctx->tz;
+        const bool own_tile = ctx->active_kernel == RTPN_KERNEL_WINDOW;
+        w.tx = own_tile ? ctx->tx : 0;
+        w.ty = own_tile ? ctx->ty : 0;
+        w.tz = own_tile ? ctx->tz : 0;
         int rc = launch_window(ctx->N, ctx->prec, w, st);
         if (rc) return fail(ctx, RTPN_ECUDA, std::string("window kernel: ") +
                                                  cudaGetErrorString((cudaError_t)rc));
@@ -158,7 +160,37 @@ int run_pass(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st) {
     return RTPN_OK;
 }
 
-int enqueue_pairs(rtpn_ctx* ctx, int pairs, cudaStream_t st) {
+// One fused pass (even full step, odd step with factors fac_odd) from state x into state y.
+int fused_pass(rtpn_ctx* ctx, const void* x, void* y, int fac_odd, cudaStream_t st) {
+    FusedLaunch f;
+    f.x = x;
+    f.y = y;
+    f.fac = (const float*)ctx->fac;
+    f.g = ctx->g;
+    f.fac_odd = fac_odd;
+    f.zc = ctx->tz;
+    int rc = launch_fused(ctx->N, ctx->prec, f, st);
+    if (rc) return fail(ctx, RTPN_ECUDA, std::string("fused kernel: ") + cudaGetErrorString((cudaError_t)rc));
+    return RTPN_OK;
+}
+
+void* other_buffer(const rtpn_ctx* ctx, const void* cur) { return cur == ctx->u ? ctx->u_alt : ctx->u; }
+
+// `pairs` fused passes alternating between the two buffers, starting from state `from`; the state
+// ends in `from` for an even count and in the other buffer for an odd one.
+int enqueue_fused(rtpn_ctx* ctx, int pairs, void* from, cudaStream_t st) {
+    void* x = from;
+    for (int p = 0; p < pairs; ++p) {
+        void* y = other_buffer(ctx, x);
+        int rc = fused_pass(ctx, x, y, FAC_FULL, st);
+        if (rc) return rc;
+        x = y;
+    }
+    return RTPN_OK;
+}
+
+int enqueue_pairs(rtpn_ctx* ctx, int pairs, bool fused, cudaStream_t st) {
+    if (fused) return enqueue_fused(ctx, pairs, ctx->u, st);
     for (int p = 0; p < pairs; ++p) {
         int rc = run_pass(ctx, 0, FAC_FULL, st);
         if (rc) return rc;
@@ -173,19 +205,28 @@ void drop_graphs(rtpn_ctx* ctx) {
     ctx->graphs.clear();
 }
 
-// (even, odd) full-step pairs, replayed from cached graphs of 64 / 8 / 1 pairs
-int launch_pairs(rtpn_ctx* ctx, int pairs) {
+// (even, odd) full-step pairs, replayed from cached graphs of 64 / 8 / 1 pairs.  Fused passes
+// alternate between the two state buffers: their graphs are keyed by which buffer they start from
+// (the buffer addresses are fixed for the life of the context) and ctx->u follows the state.
+// `fused` = false runs the two-pass schedule (also with RTPN_KERNEL_FUSED active).
+int launch_pairs(rtpn_ctx* ctx, int pairs, bool fused) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CUDA_TRY(ctx, cudaStreamIsCapturing(ctx->stream, &cap));
-    if (cap != cudaStreamCaptureStatusNone) return enqueue_pairs(ctx, pairs, ctx->stream);
+    if (cap != cudaStreamCaptureStatusNone) {
+        int rc = enqueue_pairs(ctx, pairs, fused, ctx->stream);
+        if (!rc && fused && (pairs & 1)) std::swap(ctx->u, ctx->u_alt);
+        return rc;
+    }
     const int sizes[3] = {64, 8, 1};
     for (int s : sizes) {
         while (pairs >= s) {
-            auto it = ctx->graphs.find(s);
+            // key: pair count, plus 1 << 20 for fused graphs starting from the second buffer
+            const int key = fused ? s + (1 << 16) + (ctx->u == ctx->u_home ? 0 : 1 << 20) : s;
+            auto it = ctx->graphs.find(key);
             if (it == ctx->graphs.end()) {
                 cudaGraph_t graph = nullptr;
                 CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->own, cudaStreamCaptureModeThreadLocal));
-                int rc = enqueue_pairs(ctx, s, ctx->own);
+                int rc = enqueue_pairs(ctx, s, fused, ctx->own);
                 cudaError_t e = cudaStreamEndCapture(ctx->own, &graph);
                 if (rc) {
                     if (graph) cudaGraphDestroy(graph);
@@ -198,9 +239,10 @@ int launch_pairs(rtpn_ctx* ctx, int pairs) {
                 cudaGraphDestroy(graph);
                 if (e != cudaSuccess)
                     return fail(ctx, RTPN_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
-                it = ctx->graphs.emplace(s, exec).first;
+                it = ctx->graphs.emplace(key, exec).first;
             }
             CUDA_TRY(ctx, cudaGraphLaunch(it->second, ctx->stream));
+            if (fused && (s & 1)) std::swap(ctx->u, ctx->u_alt);
             pairs -= s;
         }
     }
@@ -267,6 +309,8 @@ int upload_tables(rtpn_ctx* ctx) {
 void release(rtpn_ctx* ctx) {
     drop_graphs(ctx);
     if (ctx->u) cudaFree(ctx->u);
+    if (ctx->u_alt) cudaFree(ctx->u_alt);
+    ctx->u_alt = ctx->u_home = nullptr;
     if (ctx->fac) cudaFree(ctx->fac);
     if (ctx->table_mem) cudaFree(ctx->table_mem);
     if (ctx->partial) cudaFree(ctx->partial);
@@ -321,6 +365,22 @@ int choose_kernel(rtpn_ctx* ctx) {
         int rc = window_prepare(ctx->md, ctx->g.h, ctx->prec);
         if (rc) return fail(ctx, RTPN_ECUDA, std::string("window constants: ") +
                                                  cudaGetErrorString((cudaError_t)rc));
+    }
+    if (k == RTPN_KERNEL_FUSED) {
+        if (!fused_supported(ctx->N, ctx->prec) || !window_supported(ctx->N, ctx->prec))
+            return fail(ctx, RTPN_EUNSUPPORTED, "fused kernel not compiled for this N/precision");
+        int rc = fused_prepare(ctx->md, ctx->prec);
+        if (!rc) rc = window_prepare(ctx->md, ctx->g.h, ctx->prec);
+        if (rc) return fail(ctx, RTPN_ECUDA, std::string("fused kernel constants: ") +
+                                                 cudaGetErrorString((cudaError_t)rc));
+        if (!ctx->u_alt) {
+            cudaError_t e = cudaMalloc(&ctx->u_alt, (size_t)ctx->md.nc * ctx->g.V * ctx->elem);
+            if (e != cudaSuccess) {
+                ctx->u_alt = nullptr;
+                cudaGetLastError();
+                return fail(ctx, RTPN_ENOMEM, "second state buffer of the fused kernel");
+            }
+        }
     }
     if (k != ctx->active_kernel) drop_graphs(ctx);
     ctx->active_kernel = k;
@@ -420,6 +480,7 @@ int rtpn_create(rtpn_ctx** out, int N, int nx, int ny, int nz, double h, int bc,
     ctx->stream = ctx->own;
     cudaError_t e = cudaMalloc(&ctx->u, (size_t)ctx->md.nc * V * ctx->elem);
     if (e != cudaSuccess) return bail(fail(ctx, RTPN_ENOMEM, "state allocation failed"));
+    ctx->u_home = ctx->u;
     e = cudaMalloc(&ctx->fac, (size_t)FAC_PLANES * V * fac_elem);
     if (e != cudaSuccess) return bail(fail(ctx, RTPN_ENOMEM, "factor allocation failed"));
     e = cudaMalloc(&ctx->staging, (size_t)V * 8);
@@ -463,10 +524,13 @@ int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_
 int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z, int depth) {
     if (!ctx) return RTPN_EINVAL;
     if (depth < 0 || depth > 8) return fail(ctx, RTPN_EINVAL, "bad stage depth");
-    if (kernel < RTPN_KERNEL_AUTO || kernel > RTPN_KERNEL_STAGE)
+    if (kernel < RTPN_KERNEL_AUTO || kernel > RTPN_KERNEL_FUSED)
         return fail(ctx, RTPN_EINVAL, "unknown kernel");
     if (tile_x < 0 || tile_y < 0 || tile_z < 0) return fail(ctx, RTPN_EINVAL, "bad tile");
-    if (kernel != RTPN_KERNEL_STAGE && (tile_x || tile_y || tile_z)) {
+    if (kernel == RTPN_KERNEL_FUSED) {
+        if ((tile_x && tile_x != 32) || (tile_y && tile_y != 8))
+            return fail(ctx, RTPN_EINVAL, "the fused kernel's tile is 32 x 8 cells");
+    } else if (kernel != RTPN_KERNEL_STAGE && (tile_x || tile_y || tile_z)) {
         const long long th = (long long)(tile_x ? tile_x : 32) * (tile_y ? tile_y : 4) *
                              (tile_z ? tile_z : 2);
         if (th > 256 || th % 32 != 0)
@@ -596,10 +660,22 @@ int rtpn_step(rtpn_ctx* ctx, int k) {
     if (!ctx || k < 0) return RTPN_EINVAL;
     if (!ctx->media_set) return fail(ctx, RTPN_ESTATE, "rtpn_set_media has not been called");
     if (k == 0) return RTPN_OK;
+    bool fused = ctx->active_kernel == RTPN_KERNEL_FUSED;
+    if (fused) {
+        // a caller's capture keeps the pointers it saw: the two-pass schedule stays in one buffer
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        CUDA_TRY(ctx, cudaStreamIsCapturing(ctx->stream, &cap));
+        fused = cap == cudaStreamCaptureStatusNone;
+    }
     int rc = run_pass(ctx, 1, FAC_HALF, ctx->stream);
-    if (!rc) rc = launch_pairs(ctx, k - 1);
-    if (!rc) rc = run_pass(ctx, 0, FAC_FULL, ctx->stream);
-    if (!rc) rc = run_pass(ctx, 1, FAC_HALF, ctx->stream);
+    if (!rc) rc = launch_pairs(ctx, k - 1, fused);
+    if (fused) {
+        if (!rc) rc = fused_pass(ctx, ctx->u, ctx->u_alt, FAC_HALF, ctx->stream);
+        if (!rc) std::swap(ctx->u, ctx->u_alt);
+    } else {
+        if (!rc) rc = run_pass(ctx, 0, FAC_FULL, ctx->stream);
+        if (!rc) rc = run_pass(ctx, 1, FAC_HALF, ctx->stream);
+    }
     if (!rc) ctx->steps_done += k;
     return rc;
 }

@@ -80,6 +80,22 @@ bool window_supported(int N, int precision);
 int window_prepare(const Model& md, double h, int precision);
 int launch_window(int N, int precision, const WindowLaunch& w, cudaStream_t st);
 
+// ---- fused step kernels (kernels_fused.cu, fused.cu) ----
+// One pass of the even full step and the odd step after it, from state x into state y (another
+// buffer of the same layout).
+struct FusedLaunch {
+    const void* x;          // state before the pass
+    void* y;                // state after the pass
+    const float* fac;       // factor planes
+    Geom g;
+    int fac_odd;            // FAC_FULL or FAC_HALF for the odd step
+    int zc;                 // planes per z chunk (0 = automatic)
+};
+bool fused_supported(int N, int precision);
+// uploads the coefficient constants of order N (idempotent); returns cudaError_t
+int fused_prepare(const Model& md, int precision);
+int launch_fused(int N, int precision, const FusedLaunch& f, cudaStream_t st);
+
 // transposed partner table (adjoint.cu): targets of class clsB, sources of the other class
 HostTable transposed_table(const Model& md, int clsB, double h);
 
@@ -121,6 +137,8 @@ struct rtpn_ctx {
     double dt = 0;
     size_t elem = 4;                 // bytes per stored moment
     void* u = nullptr;               // state [internal c][z][y][x]
+    void* u_alt = nullptr;           // the fused kernel's second state buffer (swaps with u per pass)
+    void* u_home = nullptr;          // the state buffer allocated at creation (fixed)
     void* fac = nullptr;             // factor planes (double for FP64, float otherwise)
     void* table_mem = nullptr;       // device partner tables (both classes)
     rtpn::PartnerTable<double> tab64[2]{};

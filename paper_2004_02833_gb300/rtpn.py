@@ -18,7 +18,7 @@ BC = {"periodic": 0, "vacuum": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 DTYPE_F64, DTYPE_F32 = 0, 1
 HOST, DEVICE = 0, 1
-KERNEL = {"auto": 0, "generic": 1, "window": 2, "stage": 3}
+KERNEL = {"auto": 0, "generic": 1, "window": 2, "stage": 3, "fused": 4}
 
 
 class RtpnError(RuntimeError):

@@ -290,3 +290,85 @@ def test_stage_wait_timeout_is_reported(cuda_device, coupling_cache):
         ctx.step(2)
         got = ctx.get_moments()
     assert rel_err(got, ref) <= TOL["fp32"]
+
+
+FUSED_CASES = [
+    # N, shape (nz, ny, nx), bc, planes per z chunk (0 = automatic), steps
+    (1, (5, 6, 7), "periodic", 0, 3),
+    (3, (9, 7, 37), "vacuum", 2, 4),
+    (5, (6, 9, 33), "periodic", 4, 2),
+    (7, (23, 29, 37), "periodic", 0, 3),
+    (7, (11, 13, 70), "vacuum", 3, 1),
+    (7, (1, 1, 1), "periodic", 0, 2),
+    (9, (5, 17, 64), "vacuum", 0, 2),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("N,shape,bc,zc,steps", FUSED_CASES)
+def test_fused_kernel(cuda_device, coupling_cache, N, shape, bc, zc, steps, precision):
+    # even full step and odd step in one pass between two buffers: ragged 32 x 8 tiles in x and y,
+    # several z chunks, zero or wrapped halos, odd and even numbers of passes (the state ends in
+    # either buffer)
+    inst, u0 = synth.random_instance(N, shape, seed=400 + N, bc=bc)
+    ref = oracle_problem(inst, coupling_cache).run(u0, steps)
+    with rtpn.Context(N, inst.shape, inst.h, inst.bc, precision, inst.dt) as ctx:
+        ctx.set_kernel("fused", (0, 0, zc))
+        assert ctx.info().kernel == 4
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        ctx.step(steps)
+        got = ctx.get_moments()
+        s0 = ctx.sum_u0()
+    assert rel_err(got, ref) <= TOL[precision], rel_err(got, ref)
+    assert abs(s0 - got[0].sum()) <= 1e-9 * max(1.0, abs(got[0]).sum())
+
+
+def test_fused_graphs_buffers_and_kernel_switch(cuda_device, coupling_cache):
+    # 73 steps replay the 64-, 8- and 1-pair graphs from both buffers; single steps and a switch
+    # back to the in-place window kernel continue from whichever buffer holds the state
+    inst, u0 = synth.random_instance(3, (6, 10, 40), seed=41, bc="vacuum")
+    P = oracle_problem(inst, coupling_cache)
+    with rtpn.Context(3, inst.shape, inst.h, inst.bc, "fp32", inst.dt) as ctx:
+        ctx.set_kernel("fused")
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        ctx.step(73)
+        ref = P.run(u0, 73)
+        assert rel_err(ctx.get_moments(), ref) <= TOL["fp32"]
+        for _ in range(3):
+            ctx.step(1)
+        ctx.step(2)
+        ref = P.run(ref, 5)
+        assert rel_err(ctx.get_moments(), ref) <= TOL["fp32"]
+        ctx.set_kernel("window")
+        ctx.step(2)
+        ref = P.run(ref, 2)
+        assert rel_err(ctx.get_moments(), ref) <= TOL["fp32"]
+        ctx.set_kernel("fused", (32, 8, 5))
+        ctx.step(3)
+        ref = P.run(ref, 3)
+        assert rel_err(ctx.get_moments(), ref) <= TOL["fp32"]
+
+
+def test_fused_matches_window_long_run(cuda_device):
+    # same per-cell arithmetic as the window kernel, 20 steps
+    inst, u0 = synth.random_instance(7, (12, 20, 64), seed=77, bc="periodic")
+    a = gpu_run(inst, u0, 20, "fp32", kernel="fused")
+    b = gpu_run(inst, u0, 20, "fp32", kernel="window")
+    assert rel_err(a, b) <= 1e-6
+
+
+def test_fused_kernel_rejections(cuda_device):
+    with rtpn.Context(15, (2, 2, 8), 0.5, "periodic", "fp32") as ctx:
+        with pytest.raises(rtpn.RtpnError) as e:
+            ctx.set_kernel("fused")
+        assert e.value.code == rtpn.EUNSUPPORTED
+    with rtpn.Context(7, (2, 2, 8), 0.5, "periodic", "fp64") as ctx:
+        with pytest.raises(rtpn.RtpnError) as e:
+            ctx.set_kernel("fused")
+        assert e.value.code == rtpn.EUNSUPPORTED
+    with rtpn.Context(7, (2, 2, 8), 0.5, "periodic", "fp32") as ctx:
+        with pytest.raises(rtpn.RtpnError) as e:
+            ctx.set_kernel("fused", (16, 8, 0))
+        assert e.value.code == rtpn.EINVAL
