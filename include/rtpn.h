@@ -152,7 +152,10 @@ int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int ti
  * of sigma over its 2^k adjacent cells (periodic: wrapped; vacuum: in-domain cells only), then
  * c = sigma_a (u_0) or sigma_a + sigma_s (all others) and the factors of Eq. (5),
  * alpha = exp(-c tau) and beta = tau E(-c tau), for tau = dt and dt/2, rounded to the storage
- * precision.  RTPN_EINVAL on NULL or bad enums; negative sigma is not checked.
+ * precision.  May be called again between steps: media and source then vary in time piecewise
+ * constantly at step resolution (the time dependence of the coefficients in Eq. 1), stream-ordered
+ * after the steps already enqueued.  RTPN_EINVAL on NULL or bad enums; negative sigma is not
+ * checked.
  */
 int rtpn_set_media(rtpn_ctx* ctx, const void* sigma_a, const void* sigma_s, const void* q,
                    int dtype, int where);

@@ -372,3 +372,22 @@ def test_fused_kernel_rejections(cuda_device):
         with pytest.raises(rtpn.RtpnError) as e:
             ctx.set_kernel("fused", (16, 8, 0))
         assert e.value.code == rtpn.EINVAL
+
+
+@pytest.mark.parametrize("N,shape,kernel", [(7, (6, 9, 40), "window"), (7, (6, 9, 40), "fused"),
+                                            (15, (5, 6, 40), "stage"), (3, (4, 5, 6), "generic")])
+def test_media_and_source_changed_between_steps(cuda_device, coupling_cache, N, shape, kernel):
+    # sigma_a, sigma_s and q piecewise constant in time: new media between two step calls (the
+    # factors are recomputed in place, so cached graphs stay valid)
+    inst_a, u0 = synth.random_instance(N, shape, seed=700 + N, bc="vacuum")
+    inst_b, _ = synth.random_instance(N, shape, seed=800 + N, bc="vacuum")
+    Pa, Pb = oracle_problem(inst_a, coupling_cache), oracle_problem(inst_b, coupling_cache)
+    ref = Pa.run(Pb.run(Pa.run(u0, 3), 4), 2)
+    with rtpn.Context(N, inst_a.shape, inst_a.h, inst_a.bc, "fp32", inst_a.dt) as ctx:
+        ctx.set_kernel(kernel)
+        ctx.set_moments(u0)
+        for inst, k in ((inst_a, 3), (inst_b, 4), (inst_a, 2)):
+            ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+            ctx.step(k)
+        got = ctx.get_moments()
+    assert rel_err(got, ref) <= TOL["fp32"], rel_err(got, ref)
