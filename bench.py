@@ -428,8 +428,17 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
                                    max(abs(res["window_u0_sum"]), 1e-300),
                 "value": 64 * V / (res["fused"] / 1e3) / 1e6, "unit": UNIT}
 
+    def reactor():
+        # the reactor-like showcase (Section 5.2) as a P_N convergence study against P39
+        from paper_2004_02833_gb300 import showcase
+
+        r = showcase.reactor_convergence(n=64, orders=(3, 7, 19, 29, 39), steps=100)
+        r.pop("log10_u0_line_ref")
+        return r
+
     out["bf16"] = _guard(bf16)
     out["fused"] = _guard(fused)
+    out["reactor"] = _guard(reactor)
     out["batched"] = _guard(batched)
     out["adjoint"] = _guard(adjoint)
     return out

@@ -13,6 +13,9 @@ Workloads (the paper has no public data set; its only geometry, the reactor show
                         checkerboard over the interior 5^3, scatterers sigma_s = 1 elsewhere,
                         a source q = 1 in u_0 on the central block), vacuum boundaries;
   * ``random_blocks``   sigma_s log-uniform in [0.1, 10], constant per 8^3 block, sigma_a = 0.01;
+  * ``reactor_like``    a stand-in for the reactor showcase of Section 5.2: fuel rods 5 cells
+                        (1 length unit) thick with source q = 2 in water (sigma_a = 10) inside a
+                        concrete shell (sigma_a = 5), sigma_s = 1 everywhere, vacuum boundaries;
   * ``random_state`` / ``random_media``  dense random fields for parity tests.
 """
 from __future__ import annotations
@@ -113,6 +116,39 @@ def random_blocks(N: int, n: int, seed: int = 2, block: int = 8, name: str = "ra
     shape = (n, n, n)
     return Instance(N, shape, h, 0.3 * h, "periodic", np.full(shape, 0.01), ss,
                     np.zeros(shape), gaussian(n, 0.1), name)
+
+
+def reactor_media(n: int, shell: int | None = None, rod: int = 5, pitch: int = 10):
+    """sigma_a, sigma_s, q of the reactor-like cube at n^3 cells.
+
+    The paper's figure of the geometry is not available, so this is a reading of its text: a
+    concrete shell of `shell` cells (default n // 16, at least 1) on every face (sigma_a = 5); inside
+    it water (sigma_a = 10); a core in the middle half of the inner box in x and y and its middle
+    three quarters in z holds fuel rods along z, `rod` x `rod` cells each on a `pitch`-cell lattice
+    (source q = 2, no absorption).  sigma_s = 1 everywhere.
+    """
+    shell = max(1, n // 16) if shell is None else shell
+    i = np.arange(n)
+    inner = (i >= shell) & (i < n - shell)
+    w = n - 2 * shell
+    core_xy = (i >= shell + w // 4) & (i < n - shell - w // 4)
+    core_z = (i >= shell + w // 8) & (i < n - shell - w // 8)
+    rod_xy = core_xy & (((i - shell - w // 4) % pitch) < rod)
+    Z, Y, X = np.meshgrid(i, i, i, indexing="ij")
+    inside = inner[Z] & inner[Y] & inner[X]
+    fuel = rod_xy[X] & rod_xy[Y] & core_z[Z] & inside
+    sigma_a = np.where(inside, 10.0, 5.0)
+    sigma_a = np.where(fuel, 0.0, sigma_a)
+    sigma_s = np.ones((n, n, n))
+    q = np.where(fuel, 2.0, 0.0)
+    return sigma_a, sigma_s, q
+
+
+def reactor_like(N: int, n: int, h: float = 0.2, name: str = "reactor_like") -> Instance:
+    """The reactor-like cube (``reactor_media``) at n^3 cells of size h (1 length unit = 5 cells),
+    dt = 0.3 h, vacuum boundaries, zero initial state."""
+    sa, ss, q = reactor_media(n)
+    return Instance(N, (n, n, n), h, 0.3 * h, "vacuum", sa, ss, q, np.zeros((n, n, n)), name)
 
 
 def batch_instances(count: int = 64, seed: int = 3, orders=(1, 3, 5, 9, 15),

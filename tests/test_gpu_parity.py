@@ -391,3 +391,30 @@ def test_media_and_source_changed_between_steps(cuda_device, coupling_cache, N, 
             ctx.step(k)
         got = ctx.get_moments()
     assert rel_err(got, ref) <= TOL["fp32"], rel_err(got, ref)
+
+
+@pytest.mark.parametrize("N", [19, 29])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_generic_kernel_at_orders_without_compiled_kernels(cuda_device, coupling_cache, N, precision):
+    # P19 and P29 (the reactor showcase's middle orders) run on the generic kernel
+    inst, u0 = synth.random_instance(N, (3, 4, 5), seed=900 + N, bc="vacuum")
+    ref = oracle_problem(inst, coupling_cache).run(u0, 2)
+    with rtpn.Context(N, inst.shape, inst.h, inst.bc, precision, inst.dt) as ctx:
+        assert ctx.info().kernel == 1
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        ctx.step(2)
+        got = ctx.get_moments()
+    assert rel_err(got, ref) <= TOL[precision], rel_err(got, ref)
+
+
+def test_reactor_showcase_converges_in_N(cuda_device):
+    # the reactor-like cube: the u_0 field of P_N approaches that of P39 as N grows
+    from paper_2004_02833_gb300 import showcase
+
+    r = showcase.reactor_convergence(n=32, orders=(3, 19, 39), steps=40)
+    e = {N: r["orders"][N]["rel_l2_vs_ref"] for N in (3, 19)}
+    assert all(np.isfinite(v) for v in e.values())
+    assert r["orders"][39]["rel_l2_vs_ref"] == 0.0
+    assert e[19] < e[3], e
+    assert r["orders"][39]["u0_total"] > 0
