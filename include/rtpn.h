@@ -87,6 +87,7 @@ typedef struct rtpn_info {
     long long steps_done;  /* full steps taken since the last set_moments    */
     int tile[3];           /* CTA tile of the active kernel (0 = not tiled)  */
     int depth;             /* stage buffers of the staged kernel (1 = other) */
+    double hy, hz;         /* cell sizes along y and z (h is the one along x) */
 } rtpn_info;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -124,6 +125,14 @@ int rtpn_create(rtpn_ctx** out, int N, int nx, int ny, int nz, double h, int bc,
 
 /* Free every device allocation of the context (after synchronising its stream). NULL is a no-op. */
 int rtpn_destroy(rtpn_ctx* ctx);
+
+/* Cell sizes along x, y and z (rtpn_create sets all three to h): the differences of Section 2.1
+ * divide by the cell size of their own axis, and dt must stay below min(hx, hy, hz)/3 (RTPN_ECFL
+ * otherwise; the spacing is then unchanged).  Non-cubic cells run on the staged and generic kernels
+ * (and the adjoint): RTPN_EUNSUPPORTED if the window or fused kernel is selected explicitly or the
+ * context is a batch instance; RTPN_KERNEL_AUTO moves to the staged or generic kernel.  Rebuilds the
+ * coupling tables (synchronises the context stream); the media factors do not depend on h. */
+int rtpn_set_spacing(rtpn_ctx* ctx, double hx, double hy, double hz);
 
 /* Order all later work of the context on `stream` (a cudaStream_t; NULL = legacy default). */
 int rtpn_set_stream(rtpn_ctx* ctx, void* stream);

@@ -253,7 +253,7 @@ unsigned blocks_for(long long V, int threads = 256) { return (unsigned)((V + thr
 }  // namespace
 
 // Transposed partner table of class B targets (sources = class A, the w planes), host side.
-HostTable transposed_table(const Model& md, int clsB, double h) {
+HostTable transposed_table(const Model& md, int clsB, const Geom& g) {
     HostTable t;
     t.a0 = clsB == 0 ? 0 : md.ne;
     t.na = clsB == 0 ? md.ne : md.no;
@@ -270,7 +270,7 @@ HostTable transposed_table(const Model& md, int clsB, double h) {
             const bool a_upper = ca.slot[e.axis] == 2;
             t.src.push_back(md.internal_of_abi[e.a]);
             t.code.push_back(e.axis * 2 + (a_upper ? 0 : 1));
-            t.coef.push_back((a_upper ? 1.0 : -1.0) * e.v / h);
+            t.coef.push_back((a_upper ? 1.0 : -1.0) * e.v / axis_h(g, e.axis));
         }
         t.row.push_back((int)t.src.size());
         t.fplane.push_back(0);
@@ -354,7 +354,7 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
     else
         tf = reinterpret_cast<const PartnerTable<F>*>(ctx->tab32);
     for (int c = 0; c < 2; ++c)
-        if (!tt[c].upload(transposed_table(ctx->md, c, g.h)))
+        if (!tt[c].upload(transposed_table(ctx->md, c, g)))
             return afail(ctx, RTPN_ENOMEM, "adjoint: tables");
     k_adj_factors<F><<<blocks_for(V), 256, 0, st>>>(ctx->media, ctx->media + V, (F*)dfac.p, g, ctx->dt);
 

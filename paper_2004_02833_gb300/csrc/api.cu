@@ -1,6 +1,7 @@
 // The C ABI of include/rtpn.h: context life cycle, data movement and the step schedule.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
@@ -249,7 +250,7 @@ int launch_pairs(rtpn_ctx* ctx, int pairs, bool fused) {
     return RTPN_OK;
 }
 
-HostTable host_table(const Model& md, int cls, double h) {
+HostTable host_table(const Model& md, int cls, const Geom& g) {
     HostTable t;
     t.a0 = cls == 0 ? 0 : md.ne;
     t.na = cls == 0 ? md.ne : md.no;
@@ -265,7 +266,7 @@ HostTable host_table(const Model& md, int cls, double h) {
             const bool upper = ca.slot[e.axis] == 2;  // target on a 2-slot reads cells i, i+1
             t.src.push_back(md.internal_of_abi[e.b]);
             t.code.push_back(e.axis * 2 + (upper ? 1 : 0));
-            t.coef.push_back((upper ? 1.0 : -1.0) * e.v / h);
+            t.coef.push_back((upper ? 1.0 : -1.0) * e.v / axis_h(g, e.axis));
         }
         t.row.push_back((int)t.src.size());
         t.fplane.push_back(a == 0 ? FAC_U0 : 2 * slot_code(ca.slot));
@@ -275,7 +276,7 @@ HostTable host_table(const Model& md, int cls, double h) {
 
 // upload both classes' tables into one allocation (ints, then doubles, then floats)
 int upload_tables(rtpn_ctx* ctx) {
-    HostTable t[2] = {host_table(ctx->md, 0, ctx->g.h), host_table(ctx->md, 1, ctx->g.h)};
+    HostTable t[2] = {host_table(ctx->md, 0, ctx->g), host_table(ctx->md, 1, ctx->g)};
     size_t bytes = 0;
     for (auto& x : t)
         bytes += (x.row.size() + x.src.size() + x.code.size() + x.fplane.size()) * sizeof(int) +
@@ -341,14 +342,20 @@ constexpr int kStageMinN = 15;
 
 int choose_kernel(rtpn_ctx* ctx) {
     int k = ctx->kernel;
+    const bool cubic = cubic_cells(ctx->g);
     if (k == RTPN_KERNEL_AUTO) {
+        // the window kernels' coupling constants are shared by every context of the process, so
+        // they take cubic cells only; the staged and generic kernels keep theirs per context
         const bool tile_set = ctx->tx || ctx->ty || ctx->tz;
-        if (kStageInAuto && ctx->N >= kStageMinN && stage_supported(ctx->N, ctx->prec, ctx->g.nx) &&
+        if (kStageInAuto && (ctx->N >= kStageMinN || !cubic) &&
+            stage_supported(ctx->N, ctx->prec, ctx->g.nx) &&
             (!tile_set || stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->depth, ctx->prec)))
             k = RTPN_KERNEL_STAGE;
         else
-            k = window_supported(ctx->N, ctx->prec) ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
+            k = cubic && window_supported(ctx->N, ctx->prec) ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
     }
+    if (!cubic && (k == RTPN_KERNEL_WINDOW || k == RTPN_KERNEL_FUSED))
+        return fail(ctx, RTPN_EUNSUPPORTED, "the window and fused kernels take cubic cells only");
     if (k == RTPN_KERNEL_STAGE) {
         if (!stage_supported(ctx->N, ctx->prec, ctx->g.nx))
             return fail(ctx, RTPN_EUNSUPPORTED,
@@ -463,7 +470,7 @@ int rtpn_create(rtpn_ctx** out, int N, int nx, int ny, int nz, double h, int bc,
     rtpn_ctx* ctx = new rtpn_ctx();
     ctx->md = build_model(N);
     ctx->N = N;
-    ctx->g = Geom{nx, ny, nz, V, bc, h};
+    ctx->g = Geom{nx, ny, nz, V, bc, h, h, h};
     ctx->prec = precision;
     ctx->dt = dt;
     ctx->elem = precision == RTPN_FP64 ? 8 : (precision == RTPN_FP32 ? 4 : 2);
@@ -509,6 +516,38 @@ int rtpn_destroy(rtpn_ctx* ctx) {
     release(ctx);
     delete ctx;
     return RTPN_OK;
+}
+
+int rtpn_set_spacing(rtpn_ctx* ctx, double hx, double hy, double hz) {
+    if (!ctx) return RTPN_EINVAL;
+    if (!(hx > 0.0 && hy > 0.0 && hz > 0.0) || !std::isfinite(hx) || !std::isfinite(hy) ||
+        !std::isfinite(hz))
+        return fail(ctx, RTPN_EINVAL, "cell sizes must be positive and finite");
+    if (!(ctx->dt < std::min(hx, std::min(hy, hz)) / 3.0))
+        return fail(ctx, RTPN_ECFL, "dt must be below min(hx, hy, hz)/3 (Section 2.1)");
+    const bool cubic = hx == hy && hy == hz;
+    if (!cubic && ctx->batch_member)
+        return fail(ctx, RTPN_EUNSUPPORTED, "batch instances take cubic cells only");
+    const Geom old = ctx->g;
+    ctx->g.h = hx;
+    ctx->g.hy = hy;
+    ctx->g.hz = hz;
+    auto restore = [&](int code, const std::string& msg) {
+        ctx->g = old;
+        return fail(ctx, code, msg);
+    };
+    if (!cubic && (ctx->kernel == RTPN_KERNEL_WINDOW || ctx->kernel == RTPN_KERNEL_FUSED))
+        return restore(RTPN_EUNSUPPORTED, "the window and fused kernels take cubic cells only");
+    // the partner tables and the staged kernel's constants carry the spacing: rebuild them
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->table_mem) cudaFree(ctx->table_mem);
+    ctx->table_mem = nullptr;
+    int rc = upload_tables(ctx);
+    if (rc) return rc;
+    if (ctx->stage_mem) cudaFree(ctx->stage_mem);
+    ctx->stage_mem = nullptr;
+    drop_graphs(ctx);
+    return choose_kernel(ctx);
 }
 
 int rtpn_set_stream(rtpn_ctx* ctx, void* stream) {
@@ -758,6 +797,8 @@ int rtpn_get_info(const rtpn_ctx* ctx, rtpn_info* out) {
     out->precision = ctx->prec;
     out->kernel = ctx->active_kernel;
     out->h = ctx->g.h;
+    out->hy = ctx->g.hy;
+    out->hz = ctx->g.hz;
     out->dt = ctx->dt;
     out->state_bytes = (size_t)ctx->md.nc * ctx->g.V * ctx->elem;
     out->factor_bytes = (size_t)FAC_PLANES * ctx->g.V * (ctx->prec == RTPN_FP64 ? 8 : 4);

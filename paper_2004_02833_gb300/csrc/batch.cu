@@ -298,6 +298,7 @@ int rtpn_batch_create(rtpn_batch** out, int count, const int* N, const int* nx, 
             delete b;
             return rc;
         }
+        c->batch_member = true;
         b->ctx.push_back(c);
         rc = bat::upload_constants(c->md);
         if (rc) {

@@ -145,8 +145,12 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
                         const int q = win::first_l(M, B) / 2 + j;
                         float* d = &tab[A][(((size_t)M * 2 + t) * nl + q) * stg::CPAD];
                         const float* k = &t10[(size_t)src * 10];
-                        for (int r = 0; r < 6; ++r) d[r] = k[r];      // z, x to M-1, x to M+1
-                        for (int r = 0; r < 4; ++r) d[8 + r] = k[6 + r];  // y to M-1, y to M+1
+                        // the kernel applies 1/h of x; z and y constants carry h / h_z, h / h_y
+                        // (exactly 1 for cubic cells)
+                        const double sz = ctx->g.h / ctx->g.hz, sy = ctx->g.h / ctx->g.hy;
+                        for (int r = 0; r < 2; ++r) d[r] = (float)(k[r] * sz);  // z
+                        for (int r = 2; r < 6; ++r) d[r] = k[r];                // x to M-1, x to M+1
+                        for (int r = 0; r < 4; ++r) d[8 + r] = (float)(k[6 + r] * sy);  // y to M-1, M+1
                     }
         }
         const size_t b0 = tab[0].size() * 4, b1 = tab[1].size() * 4, b2 = col.size() * 4;

@@ -27,8 +27,13 @@ struct Geom {
     int nx, ny, nz;
     long long V;   // cells
     int bc;        // RTPN_BC_*
-    double h;      // cell size
+    double h;      // cell size along x (the kernels' 1/h)
+    double hy = 0, hz = 0;  // cell sizes along y and z (equal to h for cubic cells)
 };
+
+// cell size along axis 0 (x), 1 (y) or 2 (z)
+inline double axis_h(const Geom& g, int axis) { return axis == 0 ? g.h : axis == 1 ? g.hy : g.hz; }
+inline bool cubic_cells(const Geom& g) { return g.hy == g.h && g.hz == g.h; }
 
 template <typename F>
 struct PartnerTable {
@@ -97,7 +102,7 @@ int fused_prepare(const Model& md, int precision);
 int launch_fused(int N, int precision, const FusedLaunch& f, cudaStream_t st);
 
 // transposed partner table (adjoint.cu): targets of class clsB, sources of the other class
-HostTable transposed_table(const Model& md, int clsB, double h);
+HostTable transposed_table(const Model& md, int clsB, const Geom& g);
 
 // ---- TMA-staged kernels (kernels_stage.cu, stage.cu) ----
 // nx must give 16-byte rows for the tensor maps
@@ -150,6 +155,7 @@ struct rtpn_ctx {
     cudaStream_t stream = nullptr;   // work stream (user's or own)
     cudaStream_t own = nullptr;      // private stream (capture, default work stream)
     bool media_set = false;
+    bool batch_member = false;       // created by rtpn_batch_create (its kernels take cubic cells)
     long long steps_done = 0;
     std::map<int, cudaGraphExec_t> graphs;  // pair-sequence graphs keyed by pair count
     std::string err;

@@ -33,7 +33,8 @@ class Info(ctypes.Structure):
                 ("nz", ctypes.c_int), ("bc", ctypes.c_int), ("precision", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("h", ctypes.c_double), ("dt", ctypes.c_double),
                 ("state_bytes", ctypes.c_size_t), ("factor_bytes", ctypes.c_size_t),
-                ("steps_done", ctypes.c_longlong), ("tile", ctypes.c_int * 3), ("depth", ctypes.c_int)]
+                ("steps_done", ctypes.c_longlong), ("tile", ctypes.c_int * 3), ("depth", ctypes.c_int),
+                ("hy", ctypes.c_double), ("hz", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -50,6 +51,7 @@ SIGNATURES = {
     "rtpn_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _D, _I, _I, _D]),
     "rtpn_destroy": (_I, [_P]),
     "rtpn_set_stream": (_I, [_P, _P]),
+    "rtpn_set_spacing": (_I, [_P, _D, _D, _D]),
     "rtpn_set_kernel": (_I, [_P, _I, _I, _I, _I]),
     "rtpn_set_kernel_ex": (_I, [_P, _I, _I, _I, _I, _I]),
     "rtpn_set_media": (_I, [_P, _P, _P, _P, _I, _I]),
@@ -198,6 +200,10 @@ class Context:
         _check(rc, self._p)
 
     # -- configuration
+    def set_spacing(self, hx: float, hy: float, hz: float):
+        """Cell sizes along x, y and z (non-cubic cells run on the staged and generic kernels)."""
+        self._chk(lib().rtpn_set_spacing(self._p, float(hx), float(hy), float(hz)))
+
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, an int handle, or None (the context's own stream)."""
         handle = getattr(stream, "cuda_stream", stream)

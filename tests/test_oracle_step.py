@@ -150,6 +150,26 @@ def test_single_mode_matches_symbol(N, kint, coupling_cache):
     assert np.abs(got - want).max() < 1e-13
 
 
+@pytest.mark.parametrize("N,kint", [(3, (1, 2, 3)), (7, (2, 1, 3))])
+def test_single_mode_matches_symbol_non_cubic_cells(N, kint, coupling_cache):
+    # cells hx != hy != hz on a 10 x 6 x 8 grid: each axis' difference divides by its own h
+    # (Section 2.1), so the mode's symbol carries (2i/h_d) sin(k_d h_d / 2) per axis
+    shape = (8, 6, 10)
+    h = (0.1, 0.13, 0.17)
+    sa, ss = 0.2, 0.7
+    P = _problem(N, shape, sa, ss, 0.0, h, 0.03, "periodic", coupling_cache)
+    n = (shape[2], shape[1], shape[0])
+    k = [2 * np.pi * kint[d] / (n[d] * P.h[d]) for d in range(3)]
+    G, _ = _symbol(P, k, sa, ss)
+    rng = np.random.default_rng(5)
+    uh = rng.standard_normal(P.n_c) + 1j * rng.standard_normal(P.n_c)
+    X, Y, Z = _positions(P, shape)
+    phase = np.array([np.exp(1j * (k[0] * X[a] + k[1] * Y[a] + k[2] * Z[a])) for a in range(P.n_c)])
+    got = P.run(np.real(uh[:, None, None, None] * phase), 4)
+    want = np.real((np.linalg.matrix_power(G, 4) @ uh)[:, None, None, None] * phase)
+    assert np.abs(got - want).max() < 1e-13
+
+
 @pytest.mark.parametrize("N", [1, 3, 7])
 def test_lossless_modes_have_unit_amplification(N, coupling_cache):
     # sigma = 0: every eigenvalue of the step lies on the unit circle for dt < h/3 (Section 2.1
