@@ -17,7 +17,10 @@ What is computed (paper passage in brackets):
   * the Strang step of Eq. (6):  S^o_{dt/2} o S^e_{dt} o S^o_{dt/2}, taken literally (no merging);
   * C = diag(c) with c = sigma_a for u_0 and c = sigma_a + sigma_s for every other component
     (Section 2, Sigma_tl with isotropic scattering; "c_k for k >= 1 are identical", Section 3.2);
-    q enters the u_0 equation only (isotropic source).
+    q enters the u_0 equation only (isotropic source);
+  * anisotropic scattering (optional ``scat``): Section 2's Sigma_tl = Sigma_a + Sigma_s0 -
+    Sigma_sl per moment order l, with Sigma_sl = f_l * sigma_s (f_0 = 1, so sigma_s = Sigma_s0):
+    c = sigma_a + (1 - f_l) sigma_s for a component of order l.
 
 Readings where the paper is silent:
   * media on staggered points [Section 3.2 says only "interpolated"]: the arithmetic mean of
@@ -95,6 +98,7 @@ class Problem:
     bc: str = PERIODIC
     mats: tuple = field(default=None, repr=False)
     slots: np.ndarray = field(default=None, repr=False)
+    scat: tuple = None    # f_l, l = 0..N, of anisotropic scattering (None: isotropic)
 
     def __post_init__(self):
         self.sigma_a = np.asarray(self.sigma_a, dtype=np.float64)
@@ -113,6 +117,10 @@ class Problem:
         if self.slots is None:
             self.slots = sh.placement(self.N, self.mats)
         self.cls = sh.parity_class(self.slots)
+        if self.scat is not None:
+            self.scat = tuple(float(v) for v in self.scat)
+            if len(self.scat) != self.N + 1 or self.scat[0] != 1.0:
+                raise ValueError("scat holds f_0 = 1, f_1, ..., f_N")
         self.c = self._collision()
 
     @property
@@ -120,7 +128,8 @@ class Problem:
         return (self.N + 1) ** 2
 
     def _collision(self) -> np.ndarray:
-        """c at each component's own points: sigma_a for u_0, sigma_a + sigma_s otherwise."""
+        """c at each component's own points: sigma_a for u_0, sigma_a + sigma_s otherwise
+        (sigma_a + (1 - f_l) sigma_s for a component of order l with anisotropic scattering)."""
         c = np.empty((self.n_c,) + self.sigma_a.shape, dtype=np.float64)
         tot = self.sigma_a + self.sigma_s
         cache = {}
@@ -129,9 +138,12 @@ class Problem:
             if a == 0:
                 c[a] = point_average(self.sigma_a, key, self.bc)
                 continue
-            if key not in cache:
-                cache[key] = point_average(tot, key, self.bc)
-            c[a] = cache[key]
+            l = int(np.sqrt(a))  # c = l*l + l + m
+            ck = key if self.scat is None else key + (l,)
+            if ck not in cache:
+                field_ = tot if self.scat is None else self.sigma_a + (1.0 - self.scat[l]) * self.sigma_s
+                cache[ck] = point_average(field_, key, self.bc)
+            c[a] = cache[ck]
         return c
 
     def derivative(self, u_b: np.ndarray, target_slot: int, d: int) -> np.ndarray:
@@ -242,6 +254,8 @@ class Problem:
 
     def gradient(self, u0: np.ndarray, k: int, w: np.ndarray):
         """J = sum_cells w * u_0 after k steps; returns (J, dJ/dsigma_a, dJ/dsigma_s, dJ/dq)."""
+        if self.scat is not None:
+            raise NotImplementedError("the adjoint takes isotropic scattering")
         J = float(np.sum(w * self.run(u0, k)[0]))
         lam = np.zeros((self.n_c,) + self.sigma_a.shape)
         lam[0] = w

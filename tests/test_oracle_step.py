@@ -288,3 +288,39 @@ def test_adjoint_dot_product_and_media_gradient(bc, coupling_cache):
 def test_cfl_rejected(coupling_cache):
     with pytest.raises(ValueError):
         _problem(1, (2, 2, 2), 0.0, 0.0, 0.0, 0.3, 0.1, "periodic", coupling_cache)
+
+
+@pytest.mark.parametrize("N", [3, 7])
+def test_anisotropic_scattering_decays_each_order_by_its_own_rate(N, coupling_cache):
+    # Section 2: a spatially uniform state has no transport, so each moment of order l >= 1 decays
+    # by exp(-(sigma_a + sigma_s - Sigma_sl) t) per step (Sigma_sl = f_l sigma_s) and u_0 by
+    # exp(-sigma_a t); here f_l = g^l (a Henyey-Greenstein phase function's moments).
+    shape = (3, 4, 5)
+    sa, ss, gHG = 0.3, 1.7, 0.6
+    f = tuple(gHG ** l for l in range(N + 1))
+    mats, slots = coupling_cache(N)
+    P = st.Problem(N, np.full(shape, sa), np.full(shape, ss), np.zeros(shape), 0.1, 0.03, "periodic",
+                   mats=mats, slots=slots, scat=f)
+    rng = np.random.default_rng(3)
+    amp = rng.uniform(0.5, 1.5, P.n_c)
+    u = np.broadcast_to(amp[:, None, None, None], (P.n_c,) + shape).copy()
+    k = 4
+    got = P.run(u, k)
+    t = k * P.dt
+    for a in range(P.n_c):
+        l = int(np.sqrt(a))
+        rate = sa if a == 0 else sa + (1.0 - f[l]) * ss
+        assert np.abs(got[a] - amp[a] * np.exp(-rate * t)).max() <= 1e-13 * amp[a]
+
+
+def test_isotropic_scattering_moments_reproduce_the_isotropic_step(coupling_cache):
+    # f_l = 0 for l >= 1 is isotropic scattering: the same step to the last bit
+    N, shape = 3, (4, 5, 6)
+    rng = np.random.default_rng(8)
+    sa, ss, q = rng.uniform(0, 2, shape), rng.uniform(0, 2, shape), rng.uniform(0, 1, shape)
+    mats, slots = coupling_cache(N)
+    u = rng.standard_normal(((N + 1) ** 2,) + shape)
+    a = st.Problem(N, sa, ss, q, 0.1, 0.03, "vacuum", mats=mats, slots=slots)
+    b = st.Problem(N, sa, ss, q, 0.1, 0.03, "vacuum", mats=mats, slots=slots,
+                   scat=(1.0,) + (0.0,) * N)
+    assert np.array_equal(a.run(u, 3), b.run(u, 3))
