@@ -126,6 +126,17 @@ int rtpn_create(rtpn_ctx** out, int N, int nx, int ny, int nz, double h, int bc,
 /* Free every device allocation of the context (after synchronising its stream). NULL is a no-op. */
 int rtpn_destroy(rtpn_ctx* ctx);
 
+/* Anisotropic scattering (Section 2: Sigma_tl = Sigma_a + Sigma_s0 - Sigma_sl per moment order l):
+ * Sigma_sl = f[l] * sigma_s with f[0] = 1 (sigma_s is Sigma_s0) and -1 <= f[l] <= 1, count = N + 1
+ * (e.g. f[l] = g^l for a Henyey-Greenstein phase function); f = NULL or count = 0 restores isotropic
+ * scattering.  Components of order l then decay by sigma_a + (1 - f[l]) sigma_s (mean over the
+ * cells adjacent to their sub-grid point, as for isotropic media).  Runs on the generic kernel only:
+ * RTPN_EUNSUPPORTED if another kernel is selected explicitly, for a batch instance, and later for
+ * rtpn_adjoint; RTPN_KERNEL_AUTO moves to the generic kernel.  Allocates 32 (N + 1) more factor
+ * planes (RTPN_ENOMEM leaves the context unchanged) and recomputes the factors of the media already
+ * set; synchronises the context stream.  RTPN_EINVAL on a bad count or f. */
+int rtpn_set_scattering(rtpn_ctx* ctx, const double* f, int count);
+
 /* Cell sizes along x, y and z (rtpn_create sets all three to h): the differences of Section 2.1
  * divide by the cell size of their own axis, and dt must stay below min(hx, hy, hz)/3 (RTPN_ECFL
  * otherwise; the spacing is then unchanged).  Non-cubic cells run on the staged and generic kernels

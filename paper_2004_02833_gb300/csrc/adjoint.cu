@@ -458,6 +458,7 @@ extern "C" int rtpn_adjoint(rtpn_ctx* ctx, const void* w, int dtype, int where, 
         (out_where != RTPN_HOST && out_where != RTPN_DEVICE))
         return afail(ctx, RTPN_EINVAL, "adjoint: bad dtype/where");
     if (ctx->prec == RTPN_BF16) return afail(ctx, RTPN_EUNSUPPORTED, "adjoint: BF16 storage");
+    if (ctx->scat) return afail(ctx, RTPN_EUNSUPPORTED, "adjoint: anisotropic scattering");
     if (!ctx->media_set || !ctx->media) return afail(ctx, RTPN_ESTATE, "adjoint: media not set");
     const long long V = ctx->g.V;
     // the weights and outputs as FP64 device arrays

@@ -147,12 +147,15 @@ int run_pass(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st) {
         if (rc) return fail(ctx, RTPN_ECUDA, std::string("window kernel: ") +
                                                  cudaGetErrorString((cudaError_t)rc));
     } else if (ctx->prec == RTPN_FP64) {
+        if (ctx->scat && fac_ofs == FAC_HALF) fac_ofs = aniso_half_ofs(ctx->N);
         launch_substep_generic<double, double>((double*)ctx->u, (const double*)ctx->fac,
                                                ctx->tab64[cls], ctx->g, fac_ofs, st);
     } else if (ctx->prec == RTPN_FP32) {
+        if (ctx->scat && fac_ofs == FAC_HALF) fac_ofs = aniso_half_ofs(ctx->N);
         launch_substep_generic<float, float>((float*)ctx->u, (const float*)ctx->fac,
                                              ctx->tab32[cls], ctx->g, fac_ofs, st);
     } else {
+        if (ctx->scat && fac_ofs == FAC_HALF) fac_ofs = aniso_half_ofs(ctx->N);
         launch_substep_generic<__nv_bfloat16, float>((__nv_bfloat16*)ctx->u,
                                                      (const float*)ctx->fac, ctx->tab32[cls],
                                                      ctx->g, fac_ofs, st);
@@ -250,7 +253,7 @@ int launch_pairs(rtpn_ctx* ctx, int pairs, bool fused) {
     return RTPN_OK;
 }
 
-HostTable host_table(const Model& md, int cls, const Geom& g) {
+HostTable host_table(const Model& md, int cls, const Geom& g, bool aniso) {
     HostTable t;
     t.a0 = cls == 0 ? 0 : md.ne;
     t.na = cls == 0 ? md.ne : md.no;
@@ -269,14 +272,16 @@ HostTable host_table(const Model& md, int cls, const Geom& g) {
             t.coef.push_back((upper ? 1.0 : -1.0) * e.v / axis_h(g, e.axis));
         }
         t.row.push_back((int)t.src.size());
-        t.fplane.push_back(a == 0 ? FAC_U0 : 2 * slot_code(ca.slot));
+        t.fplane.push_back(a == 0 ? FAC_U0
+                                  : aniso ? aniso_plane(md.N, slot_code(ca.slot), ca.l) : 2 * slot_code(ca.slot));
     }
     return t;
 }
 
 // upload both classes' tables into one allocation (ints, then doubles, then floats)
 int upload_tables(rtpn_ctx* ctx) {
-    HostTable t[2] = {host_table(ctx->md, 0, ctx->g), host_table(ctx->md, 1, ctx->g)};
+    const bool aniso = ctx->scat != nullptr;
+    HostTable t[2] = {host_table(ctx->md, 0, ctx->g, aniso), host_table(ctx->md, 1, ctx->g, aniso)};
     size_t bytes = 0;
     for (auto& x : t)
         bytes += (x.row.size() + x.src.size() + x.code.size() + x.fplane.size()) * sizeof(int) +
@@ -313,6 +318,8 @@ void release(rtpn_ctx* ctx) {
     if (ctx->u_alt) cudaFree(ctx->u_alt);
     ctx->u_alt = ctx->u_home = nullptr;
     if (ctx->fac) cudaFree(ctx->fac);
+    if (ctx->scat) cudaFree(ctx->scat);
+    ctx->scat = nullptr;
     if (ctx->table_mem) cudaFree(ctx->table_mem);
     if (ctx->partial) cudaFree(ctx->partial);
     if (ctx->counter) cudaFree(ctx->counter);
@@ -343,6 +350,12 @@ constexpr int kStageMinN = 15;
 int choose_kernel(rtpn_ctx* ctx) {
     int k = ctx->kernel;
     const bool cubic = cubic_cells(ctx->g);
+    if (ctx->scat) {
+        // per-order factors are read through the generic kernel's per-target plane table only
+        if (k != RTPN_KERNEL_AUTO && k != RTPN_KERNEL_GENERIC)
+            return fail(ctx, RTPN_EUNSUPPORTED, "anisotropic scattering runs on the generic kernel only");
+        k = RTPN_KERNEL_GENERIC;
+    }
     if (k == RTPN_KERNEL_AUTO) {
         // the window kernels' coupling constants are shared by every context of the process, so
         // they take cubic cells only; the staged and generic kernels keep theirs per context
@@ -550,6 +563,69 @@ int rtpn_set_spacing(rtpn_ctx* ctx, double hx, double hy, double hz) {
     return choose_kernel(ctx);
 }
 
+int rtpn_set_scattering(rtpn_ctx* ctx, const double* f, int count) {
+    if (!ctx) return RTPN_EINVAL;
+    const bool iso = f == nullptr || count == 0;
+    if (!iso) {
+        if (count != ctx->N + 1) return fail(ctx, RTPN_EINVAL, "give f_0 .. f_N (count = N + 1)");
+        if (f[0] != 1.0) return fail(ctx, RTPN_EINVAL, "f_0 must be 1 (Sigma_s0 = sigma_s)");
+        for (int l = 1; l <= ctx->N; ++l)
+            if (!(f[l] >= -1.0 && f[l] <= 1.0)) return fail(ctx, RTPN_EINVAL, "f_l must lie in [-1, 1]");
+        if (ctx->batch_member)
+            return fail(ctx, RTPN_EUNSUPPORTED, "batch instances take isotropic scattering only");
+        if (ctx->kernel != RTPN_KERNEL_AUTO && ctx->kernel != RTPN_KERNEL_GENERIC)
+            return fail(ctx, RTPN_EUNSUPPORTED, "anisotropic scattering runs on the generic kernel only");
+    }
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    const long long V = ctx->g.V;
+    const size_t fac_elem = ctx->prec == RTPN_FP64 ? 8 : 4;
+    const int planes = iso ? FAC_PLANES : aniso_planes(ctx->N);
+    // new buffers first, so that a failed allocation leaves the context as it was
+    double* scat = nullptr;
+    void* fac = nullptr;
+    if (!iso) {
+        cudaError_t e = cudaMalloc(&scat, sizeof(double) * (ctx->N + 1));
+        if (e == cudaSuccess) e = cudaMemcpy(scat, f, sizeof(double) * (ctx->N + 1), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (scat) cudaFree(scat);
+            cudaGetLastError();
+            return fail(ctx, RTPN_ENOMEM, "scattering moments");
+        }
+    }
+    if (planes != ctx->fac_planes) {
+        cudaError_t e = cudaMalloc(&fac, (size_t)planes * V * fac_elem);
+        if (e != cudaSuccess) {
+            if (scat) cudaFree(scat);
+            cudaGetLastError();
+            return fail(ctx, RTPN_ENOMEM, "factor planes of anisotropic scattering");
+        }
+    }
+    if (ctx->scat) cudaFree(ctx->scat);
+    ctx->scat = scat;
+    if (fac) {
+        cudaFree(ctx->fac);
+        ctx->fac = fac;
+        ctx->fac_planes = planes;
+    }
+    drop_graphs(ctx);
+    if (ctx->table_mem) cudaFree(ctx->table_mem);
+    ctx->table_mem = nullptr;
+    int rc = upload_tables(ctx);
+    if (!rc) rc = choose_kernel(ctx);
+    if (!rc && ctx->media_set) {  // the factors of the media already set, with the new moments
+        const double* m = ctx->media;
+        if (ctx->prec == RTPN_FP64)
+            launch_media_factors<double>(m, m + V, m + 2 * V, (double*)ctx->fac, ctx->g, ctx->dt,
+                                         ctx->scat, ctx->N, ctx->stream);
+        else
+            launch_media_factors<float>(m, m + V, m + 2 * V, (float*)ctx->fac, ctx->g, ctx->dt,
+                                        ctx->scat, ctx->N, ctx->stream);
+        CUDA_TRY(ctx, cudaGetLastError());
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return rc;
+}
+
 int rtpn_set_stream(rtpn_ctx* ctx, void* stream) {
     if (!ctx) return RTPN_EINVAL;
     ctx->stream = stream ? (cudaStream_t)stream : ctx->own;
@@ -628,10 +704,10 @@ int rtpn_set_media(rtpn_ctx* ctx, const void* sigma_a, const void* sigma_s, cons
     if (!rc) {
         if (ctx->prec == RTPN_FP64)
             launch_media_factors<double>(m, m + V, m + 2 * V, (double*)ctx->fac, ctx->g, ctx->dt,
-                                         ctx->stream);
+                                         ctx->scat, ctx->N, ctx->stream);
         else
             launch_media_factors<float>(m, m + V, m + 2 * V, (float*)ctx->fac, ctx->g, ctx->dt,
-                                        ctx->stream);
+                                        ctx->scat, ctx->N, ctx->stream);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = fail(ctx, RTPN_ECUDA, cudaGetErrorString(e));
     }
@@ -801,7 +877,7 @@ int rtpn_get_info(const rtpn_ctx* ctx, rtpn_info* out) {
     out->hz = ctx->g.hz;
     out->dt = ctx->dt;
     out->state_bytes = (size_t)ctx->md.nc * ctx->g.V * ctx->elem;
-    out->factor_bytes = (size_t)FAC_PLANES * ctx->g.V * (ctx->prec == RTPN_FP64 ? 8 : 4);
+    out->factor_bytes = (size_t)ctx->fac_planes * ctx->g.V * (ctx->prec == RTPN_FP64 ? 8 : 4);
     out->steps_done = ctx->steps_done;
     out->tile[0] = ctx->tx;
     out->tile[1] = ctx->ty;

@@ -117,7 +117,7 @@ __device__ __forceinline__ void factors(double c, double tau, double* al, double
 template <typename F>
 __global__ void k_media_factors(const double* __restrict__ sa, const double* __restrict__ ss,
                                 const double* __restrict__ q, F* __restrict__ fac, Geom g,
-                                double dt) {
+                                double dt, const double* __restrict__ scat, int N) {
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= g.V) return;
     const int x = (int)(cell % g.nx);
@@ -127,7 +127,7 @@ __global__ void k_media_factors(const double* __restrict__ sa, const double* __r
         const int gx = code & 1, gy = (code >> 1) & 1, gz = (code >> 2) & 1;
         // mean of sigma_a + sigma_s over the cells adjacent to the staggered point: cell + {0,1}
         // along every axis whose slot is 2 (periodic: wrapped; vacuum: in-domain cells only)
-        double sum = 0.0;
+        double sum = 0.0, sum_a = 0.0, sum_s = 0.0;
         int cnt = 0;
         for (int dz = 0; dz <= gz; ++dz)
             for (int dy = 0; dy <= gy; ++dy)
@@ -141,8 +141,26 @@ __global__ void k_media_factors(const double* __restrict__ sa, const double* __r
                     }
                     const long long j = cell_index(g, xx, yy, zz);
                     sum += sa[j] + ss[j];
+                    sum_a += sa[j];
+                    sum_s += ss[j];
                     ++cnt;
                 }
+        if (scat) {
+            // orders l >= 1 of the slot's class (an even count of 2-slots: even l), Section 2's
+            // Sigma_tl = sigma_a + (1 - f_l) sigma_s from the point means
+            const int cls = (gx + gy + gz) & 1;
+            for (int l = cls == 0 ? 2 : 1; l <= N; l += 2) {
+                const double cl = (sum_a + (1.0 - scat[l]) * sum_s) / cnt;
+                double al, be;
+                factors(cl, dt, &al, &be);
+                const int p = aniso_plane(N, code, l);
+                fac[(long long)p * g.V + cell] = (F)al;
+                fac[(long long)(p + 1) * g.V + cell] = (F)be;
+                factors(cl, 0.5 * dt, &al, &be);
+                fac[(long long)(p + aniso_half_ofs(N)) * g.V + cell] = (F)al;
+                fac[(long long)(p + aniso_half_ofs(N) + 1) * g.V + cell] = (F)be;
+            }
+        }
         const double c = sum / cnt;
         double al, be;
         factors(c, dt, &al, &be);
@@ -161,15 +179,15 @@ __global__ void k_media_factors(const double* __restrict__ sa, const double* __r
 
 template <typename F>
 void launch_media_factors(const double* sa, const double* ss, const double* q, F* fac,
-                          const Geom& g, double dt, cudaStream_t stream) {
+                          const Geom& g, double dt, const double* scat, int N, cudaStream_t stream) {
     const int bs = 256;
     const long long nb = (g.V + bs - 1) / bs;
-    k_media_factors<F><<<(unsigned)nb, bs, 0, stream>>>(sa, ss, q, fac, g, dt);
+    k_media_factors<F><<<(unsigned)nb, bs, 0, stream>>>(sa, ss, q, fac, g, dt, scat, N);
 }
 template void launch_media_factors<double>(const double*, const double*, const double*, double*,
-                                           const Geom&, double, cudaStream_t);
+                                           const Geom&, double, const double*, int, cudaStream_t);
 template void launch_media_factors<float>(const double*, const double*, const double*, float*,
-                                          const Geom&, double, cudaStream_t);
+                                          const Geom&, double, const double*, int, cudaStream_t);
 
 // ------------------------------------------------------------------ conversions
 template <typename A, typename B>

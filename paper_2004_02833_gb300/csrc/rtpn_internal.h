@@ -22,6 +22,11 @@ constexpr int FAC_FULL = 0;    // tau = dt:   alpha at 2g, beta at 2g+1         
 constexpr int FAC_HALF = 16;   // tau = dt/2: alpha at 16+2g, beta at 17+2g      (planes 16..31)
 constexpr int FAC_U0 = 32;     // u_0 (c = sigma_a), tau = dt: alpha, beta, beta*q (planes 32..34)
 constexpr int FAC_PLANES = 35;
+// Anisotropic scattering (generic kernel only): after the 35 planes above, alpha and beta of every
+// (slot code g, order l) at tau = dt, then the same at tau = dt/2 (offset aniso_half_ofs(N)).
+__host__ __device__ inline int aniso_plane(int N, int g, int l) { return FAC_PLANES + 2 * (g * (N + 1) + l); }
+__host__ __device__ inline int aniso_half_ofs(int N) { return 16 * (N + 1); }
+__host__ __device__ inline int aniso_planes(int N) { return FAC_PLANES + 32 * (N + 1); }
 
 struct Geom {
     int nx, ny, nz;
@@ -59,9 +64,10 @@ void note_error(const std::string& msg);
 template <typename S, typename F>
 void launch_substep_generic(S* u, const F* fac, const PartnerTable<F>& tab, const Geom& g,
                             int fac_ofs, cudaStream_t st);
+// scat: f_l (l = 0..N, device) of anisotropic scattering, or nullptr (isotropic: 35 planes only)
 template <typename F>
 void launch_media_factors(const double* sa, const double* ss, const double* q, F* fac,
-                          const Geom& g, double dt, cudaStream_t st);
+                          const Geom& g, double dt, const double* scat, int N, cudaStream_t st);
 template <typename Sin, typename Sout>
 void launch_convert(const Sin* in, Sout* out, long long n, cudaStream_t st);
 template <typename S>
@@ -156,6 +162,8 @@ struct rtpn_ctx {
     cudaStream_t own = nullptr;      // private stream (capture, default work stream)
     bool media_set = false;
     bool batch_member = false;       // created by rtpn_batch_create (its kernels take cubic cells)
+    double* scat = nullptr;          // f_l (l = 0..N) of anisotropic scattering on the device, or null
+    int fac_planes = rtpn::FAC_PLANES;  // factor planes allocated
     long long steps_done = 0;
     std::map<int, cudaGraphExec_t> graphs;  // pair-sequence graphs keyed by pair count
     std::string err;

@@ -52,6 +52,7 @@ SIGNATURES = {
     "rtpn_destroy": (_I, [_P]),
     "rtpn_set_stream": (_I, [_P, _P]),
     "rtpn_set_spacing": (_I, [_P, _D, _D, _D]),
+    "rtpn_set_scattering": (_I, [_P, _P, _I]),
     "rtpn_set_kernel": (_I, [_P, _I, _I, _I, _I]),
     "rtpn_set_kernel_ex": (_I, [_P, _I, _I, _I, _I, _I]),
     "rtpn_set_media": (_I, [_P, _P, _P, _P, _I, _I]),
@@ -200,6 +201,15 @@ class Context:
         _check(rc, self._p)
 
     # -- configuration
+    def set_scattering(self, f=None):
+        """Anisotropic scattering moments f_l = Sigma_sl / sigma_s, l = 0..N (f_0 = 1); None restores
+        isotropic scattering (generic kernel only)."""
+        if f is None:
+            self._chk(lib().rtpn_set_scattering(self._p, None, 0))
+            return
+        arr = np.ascontiguousarray(f, dtype=np.float64)
+        self._chk(lib().rtpn_set_scattering(self._p, arr.ctypes.data_as(_P), int(arr.size)))
+
     def set_spacing(self, hx: float, hy: float, hz: float):
         """Cell sizes along x, y and z (non-cubic cells run on the staged and generic kernels)."""
         self._chk(lib().rtpn_set_spacing(self._p, float(hx), float(hy), float(hz)))
