@@ -140,8 +140,9 @@ int rtpn_set_scattering(rtpn_ctx* ctx, const double* f, int count);
 /* Cell sizes along x, y and z (rtpn_create sets all three to h): the differences of Section 2.1
  * divide by the cell size of their own axis, and dt must stay below min(hx, hy, hz)/3 (RTPN_ECFL
  * otherwise; the spacing is then unchanged).  Non-cubic cells run on the staged and generic kernels
- * (and the adjoint): RTPN_EUNSUPPORTED if the window or fused kernel is selected explicitly or the
- * context is a batch instance; RTPN_KERNEL_AUTO moves to the staged or generic kernel.  Rebuilds the
+ * (and the adjoint): RTPN_EUNSUPPORTED if the window or fused kernel is selected explicitly, and
+ * for a batch instance (its spacing is fixed at rtpn_batch_create); RTPN_KERNEL_AUTO moves to the
+ * staged or generic kernel.  Rebuilds the
  * coupling tables (synchronises the context stream); the media factors do not depend on h. */
 int rtpn_set_spacing(rtpn_ctx* ctx, double hx, double hy, double hz);
 

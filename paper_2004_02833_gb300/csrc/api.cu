@@ -539,8 +539,9 @@ int rtpn_set_spacing(rtpn_ctx* ctx, double hx, double hy, double hz) {
     if (!(ctx->dt < std::min(hx, std::min(hy, hz)) / 3.0))
         return fail(ctx, RTPN_ECFL, "dt must be below min(hx, hy, hz)/3 (Section 2.1)");
     const bool cubic = hx == hy && hy == hz;
-    if (!cubic && ctx->batch_member)
-        return fail(ctx, RTPN_EUNSUPPORTED, "batch instances take cubic cells only");
+    // a batch keeps each instance's 1/h in its launch items, built at creation
+    if (ctx->batch_member)
+        return fail(ctx, RTPN_EUNSUPPORTED, "the spacing of a batch instance is fixed at creation");
     const Geom old = ctx->g;
     ctx->g.h = hx;
     ctx->g.hy = hy;
