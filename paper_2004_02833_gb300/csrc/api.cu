@@ -387,6 +387,9 @@ int choose_kernel(rtpn_ctx* ctx) {
                                                  cudaGetErrorString((cudaError_t)rc));
     }
     if (k == RTPN_KERNEL_FUSED) {
+        // a batch keeps each instance's state pointer in its launch items; the fused kernel moves it
+        if (ctx->batch_member)
+            return fail(ctx, RTPN_EUNSUPPORTED, "batch instances keep their state in one buffer");
         if (!fused_supported(ctx->N, ctx->prec) || !window_supported(ctx->N, ctx->prec))
             return fail(ctx, RTPN_EUNSUPPORTED, "fused kernel not compiled for this N/precision");
         int rc = fused_prepare(ctx->md, ctx->prec);
