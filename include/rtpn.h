@@ -155,9 +155,11 @@ int rtpn_set_stream(rtpn_ctx* ctx, void* stream);
  * N (RTPN_EUNSUPPORTED otherwise).  RTPN_KERNEL_FUSED: the CTA tile is fixed at 32 x 8 cells, so
  * tile_x and tile_y must be 0 (or 32 and 8); tile_z is the number of z planes a CTA streams through
  * (0 = one wave of resident CTAs).  Selecting it allocates a second state buffer (RTPN_ENOMEM if
- * that fails); RTPN_EUNSUPPORTED for a batch instance.  RTPN_KERNEL_AUTO picks STAGE (for N >= 15), then WINDOW, then GENERIC.
- * RTPN_EUNSUPPORTED if the kernel is not compiled for (N, precision, nx); the previous selection
- * then stays. */
+ * that fails); RTPN_EUNSUPPORTED for a batch instance.
+ * RTPN_KERNEL_AUTO picks STAGE (for N >= 15), then WINDOW, then GENERIC; with non-cubic cells STAGE
+ * (any compiled N), else GENERIC; with anisotropic scattering GENERIC.
+ * RTPN_EUNSUPPORTED if the kernel is not compiled for (N, precision, nx) or does not take the
+ * context's cells or scattering; the previous selection then stays. */
 int rtpn_set_kernel(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int tile_z);
 
 /* As rtpn_set_kernel, and for RTPN_KERNEL_STAGE the pipeline depth: the number of shared-memory
