@@ -75,3 +75,9 @@ def test_create_validates_before_touching_the_device(rtpn_lib):
     with pytest.raises(rtpn.RtpnError) as e:
         rtpn.Context(3, (0, 4, 4), 0.1)
     assert e.value.code == rtpn.EINVAL
+
+
+def test_new_entry_points_reject_a_null_context(rtpn_lib):
+    # no GPU needed: argument checks come before any device call
+    assert rtpn_lib.rtpn_set_spacing(None, 0.1, 0.1, 0.1) == rtpn.EINVAL
+    assert rtpn_lib.rtpn_set_scattering(None, None, 0) == rtpn.EINVAL
