@@ -18,7 +18,8 @@
  *     matching sin(|m| phi), m = 0 is N_l^0 P_l(mu), polar axis z.
  *   - Per-cell arrays are [z][y][x] with x fastest (nx*ny*nz values).  A full state is
  *     [c][z][y][x] ((N+1)^2 * nx*ny*nz values).  A component with sub-grid slot g = 1 along an axis
- *     sits at (i + 1/2) h on that axis, g = 2 at (i + 1) h (0-based cell i).
+ *     sits at (i + 1/2) h on that axis, g = 2 at (i + 1) h (0-based cell i; h the cell size along
+ *     that axis, see rtpn_set_spacing).
  *   - `where` says whether a caller pointer is host (RTPN_HOST) or device (RTPN_DEVICE) memory.
  *     Caller buffers are never retained.  Calls with host pointers synchronise before returning;
  *     calls with device pointers are ordered on the context stream and return without waiting.
