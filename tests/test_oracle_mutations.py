@@ -1,0 +1,157 @@
+"""Mistakes planted in the oracle, one at a time, on the CPU: each must be caught by a pin that the
+unmodified oracle passes (the Fourier symbol of the staggered step, Section 2.1 and Eq. 6, on
+non-cubic cells; the closed-form decay of a uniform state, Eq. 5 and Section 2).  This shows the
+pins fix the oracle's arithmetic, not only its shape."""
+import numpy as np
+import pytest
+
+from oracle import stepper as st
+from test_oracle_step import _positions, _symbol
+
+H = (0.1, 0.13, 0.17)
+DT = 0.03
+SHAPE = (8, 6, 10)
+
+
+def _fourier_error(mats, slots, N=3, kint=(1, 2, 3), steps=3, oracle_mats=None):
+    """max |oracle - closed form| for one Fourier mode; the symbol comes from the unmodified
+    coupling matrices `mats`, the oracle runs with `oracle_mats` (default `mats`) and whatever is
+    patched in."""
+    sa, ss = 0.2, 0.7
+    z = np.zeros(SHAPE)
+    P = st.Problem(N, z + sa, z + ss, z, H, DT, "periodic", mats=mats if oracle_mats is None else oracle_mats,
+                   slots=slots)
+    n = (SHAPE[2], SHAPE[1], SHAPE[0])
+    k = [2 * np.pi * kint[d] / (n[d] * H[d]) for d in range(3)]
+    ref = st.Problem(N, z + sa, z + ss, z, H, DT, "periodic", mats=tuple(m.copy() for m in mats),
+                     slots=slots)
+    G, _ = _symbol(ref, k, sa, ss)
+    rng = np.random.default_rng(11)
+    uh = rng.standard_normal(P.n_c) + 1j * rng.standard_normal(P.n_c)
+    X, Y, Z = _positions(ref, SHAPE)
+    phase = np.array([np.exp(1j * (k[0] * X[a] + k[1] * Y[a] + k[2] * Z[a])) for a in range(P.n_c)])
+    got = P.run(np.real(uh[:, None, None, None] * phase), steps)
+    want = np.real((np.linalg.matrix_power(G, steps) @ uh)[:, None, None, None] * phase)
+    return float(np.abs(got - want).max())
+
+
+def _decay_error(mats, slots, N=3, scat=None):
+    """max relative deviation of a uniform state from its closed-form per-order decay."""
+    sa, ss = 0.3, 1.7
+    shape = (3, 4, 5)
+    P = st.Problem(N, np.full(shape, sa), np.full(shape, ss), np.zeros(shape), 0.1, DT, "periodic",
+                   mats=mats, slots=slots, scat=scat)
+    amp = np.random.default_rng(3).uniform(0.5, 1.5, P.n_c)
+    got = P.run(np.broadcast_to(amp[:, None, None, None], (P.n_c,) + shape).copy(), 4)
+    t = 4 * DT
+    f = scat if scat is not None else (1.0,) + (0.0,) * N
+    err = 0.0
+    for a in range(P.n_c):
+        l = int(np.sqrt(a))
+        rate = sa if a == 0 else sa + (1.0 - f[l]) * ss
+        err = max(err, float(np.abs(got[a] - amp[a] * np.exp(-rate * t)).max() / amp[a]))
+    return err
+
+
+def _swap_direction(self, u_b, target_slot, d):
+    if target_slot != 2:
+        return (st.shift(u_b, d, +1, self.bc) - u_b) / self.h[d]
+    return (u_b - st.shift(u_b, d, -1, self.bc)) / self.h[d]
+
+
+def _no_h(self, u_b, target_slot, d):
+    if target_slot == 2:
+        return st.shift(u_b, d, +1, self.bc) - u_b
+    return u_b - st.shift(u_b, d, -1, self.bc)
+
+
+def _h_of_x_everywhere(self, u_b, target_slot, d):
+    if target_slot == 2:
+        return (st.shift(u_b, d, +1, self.bc) - u_b) / self.h[0]
+    return (u_b - st.shift(u_b, d, -1, self.bc)) / self.h[0]
+
+
+def _classes_swapped(self, u):
+    u = self.substep(u, 0, 0.5 * self.dt)
+    u = self.substep(u, 1, self.dt)
+    return self.substep(u, 0, 0.5 * self.dt)
+
+
+def _full_odd_steps(self, u):
+    u = self.substep(u, 1, self.dt)
+    u = self.substep(u, 0, self.dt)
+    return self.substep(u, 1, self.dt)
+
+
+def _explicit_euler(self, u, cls, tau):
+    out = u.copy()
+    for a in np.nonzero(self.cls == cls)[0]:
+        out[a] = u[a] + tau * (self.residual(u, a) - self.c[a] * u[a])
+    return out
+
+
+def _dropped_source_term(self, u, a):
+    r = np.zeros(u.shape[1:])
+    for d in range(3):
+        row = self.mats[d][a]
+        for b in np.nonzero(row)[0][:-1]:  # the last coupling of every row is lost
+            r -= row[b] * self.derivative(u[b], self.slots[a, d], d)
+    return r
+
+
+FOURIER_MUTATIONS = [
+    ("difference direction swapped", "derivative", _swap_direction),
+    ("1/h dropped", "derivative", _no_h),
+    ("one cell size for every axis", "derivative", _h_of_x_everywhere),
+    ("half steps on the even class", "step", _classes_swapped),
+    ("odd substeps of full length", "step", _full_odd_steps),
+    ("Eq. 5 replaced by an explicit Euler step", "substep", _explicit_euler),
+    ("a coupling term dropped", "residual", _dropped_source_term),
+]
+
+
+def test_unmodified_oracle_passes_both_checks(coupling_cache):
+    mats, slots = coupling_cache(3)
+    assert _fourier_error(mats, slots) < 1e-13
+    assert _decay_error(mats, slots) < 1e-13
+    assert _decay_error(mats, slots, scat=tuple(0.6 ** l for l in range(4))) < 1e-13
+
+
+@pytest.mark.parametrize("name,attr,fn", FOURIER_MUTATIONS, ids=[m[0] for m in FOURIER_MUTATIONS])
+def test_planted_stepping_mistake_is_caught(coupling_cache, monkeypatch, name, attr, fn):
+    mats, slots = coupling_cache(3)
+    monkeypatch.setattr(st.Problem, attr, fn)
+    assert _fourier_error(mats, slots) > 1e-6, name
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_planted_sign_error_in_a_coupling_matrix_is_caught(coupling_cache, axis):
+    # the oracle runs with one M_d negated; the symbol keeps the true matrices
+    mats, slots = coupling_cache(3)
+    bad = tuple(-m if d == axis else m for d, m in enumerate(mats))
+    assert _fourier_error(mats, slots, oracle_mats=bad) > 1e-6
+
+
+@pytest.mark.parametrize("mistake", ["u_0 decays with sigma_s too", "per-order scattering ignored"])
+def test_planted_collision_mistake_is_caught(coupling_cache, monkeypatch, mistake):
+    mats, slots = coupling_cache(3)
+    scat = None
+    if mistake == "u_0 decays with sigma_s too":
+        orig = st.Problem._collision
+
+        def bad(self):
+            c = orig(self)
+            c[0] = st.point_average(self.sigma_a + self.sigma_s, (1, 1, 1), self.bc)
+            return c
+
+        monkeypatch.setattr(st.Problem, "_collision", bad)
+    else:
+        scat = tuple(0.6 ** l for l in range(4))
+        orig_init = st.Problem.__post_init__
+
+        def bad_init(self):
+            self.scat = None
+            orig_init(self)
+
+        monkeypatch.setattr(st.Problem, "__post_init__", bad_init)
+    assert _decay_error(mats, slots, scat=scat) > 1e-6, mistake
