@@ -1,11 +1,15 @@
 """Mistakes planted in the oracle, one at a time, on the CPU: each must be caught by a pin that the
 unmodified oracle passes (the Fourier symbol of the staggered step, Section 2.1 and Eq. 6, on
-non-cubic cells; the closed-form decay of a uniform state, Eq. 5 and Section 2).  This shows the
-pins fix the oracle's arithmetic, not only its shape."""
+non-cubic cells; the closed-form decay of a uniform state, Eq. 5 and Section 2; for the basis and
+coupling of Section 2, orthonormality, the P1 wave speeds and the Gauss nodes of the m = 0 block of
+Mz).  This shows the pins fix the oracle's arithmetic, not only its shape."""
+import math
+
 import numpy as np
 import pytest
+import scipy.special as sps
 
-from oracle import stepper as st
+from oracle import sh, stepper as st
 from test_oracle_step import _positions, _symbol
 
 H = (0.1, 0.13, 0.17)
@@ -155,3 +159,80 @@ def test_planted_collision_mistake_is_caught(coupling_cache, monkeypatch, mistak
 
         monkeypatch.setattr(st.Problem, "__post_init__", bad_init)
     assert _decay_error(mats, slots, scat=scat) > 1e-6, mistake
+
+
+# ---------------------------------------------------------------- basis and coupling (Section 2)
+def _basis_checks(N=3):
+    """(Gram error, P1 wave-speed error, Gauss-node error of the m = 0 block of Mz)."""
+    g = float(np.abs(sh.gram(N) - np.eye((N + 1) ** 2)).max())
+    Mx, My, Mz = sh.coupling(1)
+    r3 = 1.0 / math.sqrt(3.0)
+    p1 = max(abs(Mx[0, 3] - r3), abs(My[0, 1] - r3), abs(Mz[0, 2] - r3))
+    mz = sh.coupling(N)[2]
+    idx = [l * l + l for l in range(N + 1)]
+    ev = np.sort(np.linalg.eigvalsh(mz[np.ix_(idx, idx)]))
+    gw = float(np.abs(ev - np.sort(np.polynomial.legendre.leggauss(N + 1)[0])).max())
+    return g, p1, gw
+
+
+def _real_sh_variant(sqrt2=True, condon_shortley=False, swap_cos_sin=False):
+    def real_sh(N, mu, phi):
+        mu = np.asarray(mu, dtype=np.float64)
+        phi = np.asarray(phi, dtype=np.float64)
+        out = np.empty(((N + 1) ** 2,) + mu.shape)
+        for c, (l, m) in enumerate(sh.components(N)):
+            am = abs(m)
+            p = sps.lpmv(am, l, mu) * (1.0 if condon_shortley else (-1.0) ** am)
+            k = math.sqrt(2.0) if sqrt2 else 1.0
+            cos_t, sin_t = (np.sin, np.cos) if swap_cos_sin else (np.cos, np.sin)
+            if m == 0:
+                out[c] = sh._norm(l, 0) * p
+            elif m > 0:
+                out[c] = k * sh._norm(l, am) * p * cos_t(am * phi)
+            else:
+                out[c] = k * sh._norm(l, am) * p * sin_t(am * phi)
+        return out
+    return real_sh
+
+
+def _norm_without_factorials(l, m):
+    return math.sqrt((2 * l + 1) / (4.0 * math.pi))
+
+
+def _coupling_x_y_swapped(N):
+    mu, ph, w = sh.quadrature(N)
+    Y = sh.real_sh(N, mu, ph)
+    s = np.sqrt(np.maximum(0.0, 1.0 - mu * mu))
+    mats = []
+    for om in (s * np.sin(ph), s * np.cos(ph), mu):
+        M = (Y * (w * om)) @ Y.T
+        M[np.abs(M) < sh.ZERO_TOL] = 0.0
+        mats.append(M)
+    return tuple(mats)
+
+
+_orig_quadrature = sh.quadrature
+
+
+def _coarse_quadrature(N, extra=2):
+    return _orig_quadrature(max(N - 3, 0), 0)
+
+
+BASIS_MUTATIONS = [
+    ("sqrt(2) of the m != 0 functions dropped", "real_sh", _real_sh_variant(sqrt2=False)),
+    ("Condon-Shortley phase kept", "real_sh", _real_sh_variant(condon_shortley=True)),
+    ("cos and sin types swapped", "real_sh", _real_sh_variant(swap_cos_sin=True)),
+    ("(l-m)!/(l+m)! dropped from N_l^m", "_norm", _norm_without_factorials),
+    ("Omega_x and Omega_y swapped", "coupling", _coupling_x_y_swapped),
+    ("quadrature too coarse to be exact", "quadrature", _coarse_quadrature),
+]
+
+
+def test_unmodified_basis_passes_the_checks():
+    assert max(_basis_checks()) < 1e-12
+
+
+@pytest.mark.parametrize("name,attr,fn", BASIS_MUTATIONS, ids=[m[0] for m in BASIS_MUTATIONS])
+def test_planted_basis_mistake_is_caught(monkeypatch, name, attr, fn):
+    monkeypatch.setattr(sh, attr, fn)
+    assert max(_basis_checks()) > 1e-6, name
