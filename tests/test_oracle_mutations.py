@@ -236,3 +236,73 @@ def test_unmodified_basis_passes_the_checks():
 def test_planted_basis_mistake_is_caught(monkeypatch, name, attr, fn):
     monkeypatch.setattr(sh, attr, fn)
     assert max(_basis_checks()) > 1e-6, name
+
+
+# ---------------------------------------------------------------- media points and vacuum boundary
+def _interp_error():
+    """max deviation of the point mean of a linear field from its value at the staggered point."""
+    n = 6
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    sig = 1.0 + 0.5 * x + 0.25 * y + 0.125 * z
+    inner = (slice(0, n - 1),) * 3
+    err = 0.0
+    for slot in [(2, 1, 1), (1, 2, 2), (2, 2, 2)]:
+        off = [(g - 1) * 0.5 for g in slot]
+        want = 1.0 + 0.5 * (x + off[0]) + 0.25 * (y + off[1]) + 0.125 * (z + off[2])
+        err = max(err, float(np.abs(st.point_average(sig, slot, "vacuum")[inner] - want[inner]).max()))
+    return err
+
+
+def _vacuum_error(mats, slots):
+    """vacuum run against a periodic run on a padded grid whose padding is zeroed every substep."""
+    N, n = 3, 5
+    shape, pshape = (n,) * 3, (n + 2,) * 3
+    Pv = st.Problem(N, np.full(shape, 0.4), np.full(shape, 0.9), np.full(shape, 0.3), 0.2, 0.06,
+                    "vacuum", mats=mats, slots=slots)
+    Pp = st.Problem(N, np.full(pshape, 0.4), np.full(pshape, 0.9), np.full(pshape, 0.3), 0.2, 0.06,
+                    "periodic", mats=mats, slots=slots)
+    u = np.random.default_rng(5).standard_normal((Pv.n_c,) + shape)
+    up = np.zeros((Pp.n_c,) + pshape)
+    inner = (slice(None),) + (slice(1, n + 1),) * 3
+    up[inner] = u
+    for _ in range(2):
+        u = Pv.step(u)
+        for cls, tau in ((1, 0.5 * Pp.dt), (0, Pp.dt), (1, 0.5 * Pp.dt)):
+            ring = np.zeros_like(up)
+            ring[inner] = up[inner]
+            up = Pp.substep(ring, cls, tau)
+    return float(np.abs(up[inner] - u).max())
+
+
+def _point_average_lower_neighbour(sig, slot, bc):
+    total = np.array(sig, dtype=np.float64)
+    count = np.ones_like(total)
+    for d in range(3):
+        if slot[d] == 2:
+            total = total + st.shift(total, d, -1, bc)
+            count = count + st.shift(count, d, -1, bc)
+    return total / count
+
+
+_orig_shift = st.shift
+
+
+def _shift_wraps_always(f, d, s, bc):
+    return _orig_shift(f, d, s, st.PERIODIC)
+
+
+def test_unmodified_media_and_boundary_pass(coupling_cache):
+    mats, slots = coupling_cache(3)
+    assert _interp_error() < 1e-14
+    assert _vacuum_error(mats, slots) < 1e-14
+
+
+def test_planted_interpolation_mistake_is_caught(monkeypatch):
+    monkeypatch.setattr(st, "point_average", _point_average_lower_neighbour)
+    assert _interp_error() > 1e-6
+
+
+def test_planted_vacuum_mistake_is_caught(coupling_cache, monkeypatch):
+    mats, slots = coupling_cache(3)
+    monkeypatch.setattr(st, "shift", _shift_wraps_always)
+    assert _vacuum_error(mats, slots) > 1e-6
