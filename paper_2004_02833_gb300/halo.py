@@ -1,13 +1,13 @@
-"""Slab decomposition along z with one-plane halos, for running the step on several ranks.
+"""Domain decomposition with one-layer halos, for running the step on several ranks.
 
 The paper distributes the domain in blocks over MPI ranks and refreshes a one-cell ghost layer per
-face before each sweep (Section 3).  Here the unit is a slab of whole z planes per rank; before a
-substep of class A (Eq. 5 with the dual class B frozen) each rank fills its ghost planes with the
-class-B planes of its neighbours.  A half-grid difference along z reads one neighbour plane only
+face before each sweep (Section 3).  `SlabHalo` splits z into slabs of whole planes, `BlockHalo`
+splits x, y and z over a process grid; before a substep of class A (Eq. 5 with the dual class B
+frozen) each rank fills its ghost layers with the class-B layers of its neighbours.  A half-grid difference along z reads one neighbour plane only
 (Section 2.1): a target on z-slot 2 reads its sources (on z-slot 1) at i + 1, a target on z-slot 1
 reads its sources (on z-slot 2) at i - 1.  So the upper ghost plane needs only the class-B
 components on z-slot 1 and the lower one those on z-slot 2, about a quarter of the (N+1)^2 moments
-per face and substep.
+per face and substep (the same holds along x and y with the x- and y-slots).
 
 The exchange is point to point (``torch.distributed`` isend/irecv: gloo on the CPU, NCCL on GPUs),
 not a collective, and it does not depend on how the local substep is computed.  Local arrays are
@@ -110,3 +110,131 @@ class SlabHalo:
             u[up_idx, top] = recv_up
         if self.lower is not None:
             u[lo_idx, bot] = recv_lo
+
+
+def _split(n: int, parts: int) -> list[tuple[int, int]]:
+    return slabs(n, parts)
+
+
+@dataclass
+class BlockHalo:
+    """The halo of one rank's block in a px x py x pz process grid (rank = (kz * py + ky) * px + kx,
+    x fastest), the block decomposition of the paper (Section 3) with one ghost layer per face.
+    Along every axis d the upper ghost layer receives the class-B components on d-slot 1 and the
+    lower one those on d-slot 2 (`upper_sources[A][d]`, `lower_sources[A][d]`).  A difference runs
+    along one axis only, so faces suffice: edge and corner ghost cells of the state are never read
+    (the media of the whole ghosted box are input data, taken from the global arrays)."""
+
+    N: int
+    shape: tuple          # global (nz, ny, nx)
+    dims: tuple           # process grid (px, py, pz)
+    rank: int
+    periodic: bool
+
+    def __post_init__(self):
+        px, py, pz = self.dims
+        if px * py * pz < 1 or self.rank >= px * py * pz:
+            raise ValueError("rank outside the process grid")
+        self.coords = (self.rank % px, (self.rank // px) % py, self.rank // (px * py))
+        n = (self.shape[2], self.shape[1], self.shape[0])  # along x, y, z
+        self.lo_hi = [_split(n[d], self.dims[d])[self.coords[d]] for d in range(3)]
+        self.lower, self.upper = [], []
+        for d in range(3):
+            k, p = self.coords[d], self.dims[d]
+            lower = k - 1 if k > 0 else (p - 1 if self.periodic else None)
+            upper = k + 1 if k < p - 1 else (0 if self.periodic else None)
+            self.lower.append(None if lower is None else self._rank_with(d, lower))
+            self.upper.append(None if upper is None else self._rank_with(d, upper))
+        n_c = (self.N + 1) ** 2
+        info = [rtpn.component_info(self.N, c) for c in range(n_c)]
+        self.upper_sources, self.lower_sources = {}, {}
+        for A in (0, 1):
+            B = 1 - A
+            self.upper_sources[A] = [[c for c, (_, _, s, k) in enumerate(info) if k == B and s[d] == 1]
+                                     for d in range(3)]
+            self.lower_sources[A] = [[c for c, (_, _, s, k) in enumerate(info) if k == B and s[d] == 2]
+                                     for d in range(3)]
+
+    def _rank_with(self, d: int, k: int) -> int:
+        c = list(self.coords)
+        c[d] = k
+        px, py, _ = self.dims
+        return (c[2] * py + c[1]) * px + c[0]
+
+    def first(self, d: int) -> int:
+        """Local index of the first own cell along axis d (1 with a lower ghost layer)."""
+        return 1 if self.lower[d] is not None else 0
+
+    def own(self, d: int) -> int:
+        return self.lo_hi[d][1] - self.lo_hi[d][0]
+
+    def local_n(self, d: int) -> int:
+        return self.own(d) + self.first(d) + (1 if self.upper[d] is not None else 0)
+
+    def global_index(self, d: int) -> list[int]:
+        """The global cell index along axis d of every local index (ghosts wrapped when periodic)."""
+        n = (self.shape[2], self.shape[1], self.shape[0])[d]
+        return [(self.lo_hi[d][0] - self.first(d) + i) % n for i in range(self.local_n(d))]
+
+    def own_slices(self):
+        """Slices of the own cells in a local [.., z, y, x] array."""
+        return tuple(slice(self.first(d), self.first(d) + self.own(d)) for d in (2, 1, 0))
+
+    def ghost_slices(self):
+        """One index tuple per ghost face of a local [c, z, y, x] array."""
+        out = []
+        for d in range(3):
+            ax = 3 - d
+            for present, at in ((self.lower[d] is not None, 0), (self.upper[d] is not None, self.local_n(d) - 1)):
+                if present:
+                    idx = [slice(None)] * 4
+                    idx[ax] = at
+                    out.append(tuple(idx))
+        return out
+
+    def exchange(self, u, A: int, dist=None) -> None:
+        """Fills the face ghost layers of the local state `u` (torch [c][z][y][x]) that a substep of
+        class A reads, axis by axis; `dist` is torch.distributed (None: one rank only)."""
+        import torch
+
+        world = self.dims[0] * self.dims[1] * self.dims[2]
+        for d in range(3):
+            ax = 3 - d  # array axis of x, y, z in [c, z, y, x]
+            if self.lower[d] is None and self.upper[d] is None:
+                continue
+            own_lo = self.first(d)
+            own_hi = own_lo + self.own(d) - 1
+            inner = [slice(self.first(e), self.first(e) + self.own(e)) for e in range(3)]
+
+            def layer(at, comps):
+                idx = [slice(None)] * 4
+                idx[0] = torch.tensor(comps, dtype=torch.long, device=u.device)
+                for e in range(3):
+                    idx[3 - e] = at if e == d else inner[e]
+                return tuple(idx)
+
+            up_c, lo_c = self.upper_sources[A][d], self.lower_sources[A][d]
+            send_down = u[layer(own_lo, up_c)].contiguous() if self.lower[d] is not None else None
+            send_up = u[layer(own_hi, lo_c)].contiguous() if self.upper[d] is not None else None
+            recv_up = torch.empty_like(u[layer(own_lo, up_c)]) if self.upper[d] is not None else None
+            recv_lo = torch.empty_like(u[layer(own_hi, lo_c)]) if self.lower[d] is not None else None
+            if world == 1 or dist is None or self.upper[d] == self.rank:
+                # one block along a periodic axis is its own neighbour: a local copy
+                if recv_up is not None:
+                    recv_up.copy_(send_down)
+                if recv_lo is not None:
+                    recv_lo.copy_(send_up)
+            else:
+                reqs = []
+                if self.upper[d] is not None:
+                    reqs.append(dist.irecv(recv_up, src=self.upper[d], tag=2 * d))
+                    reqs.append(dist.isend(send_up, dst=self.upper[d], tag=2 * d + 1))
+                if self.lower[d] is not None:
+                    reqs.append(dist.irecv(recv_lo, src=self.lower[d], tag=2 * d + 1))
+                    reqs.append(dist.isend(send_down, dst=self.lower[d], tag=2 * d))
+                for r in reqs:
+                    r.wait()
+            if recv_up is not None:
+                u[layer(self.local_n(d) - 1, up_c)] = recv_up
+            if recv_lo is not None:
+                u[layer(0, lo_c)] = recv_lo

@@ -116,3 +116,83 @@ def test_gloo_ranks_equal_one_rank_bitwise(bc, world):
     for _, z0, z1, u in out:
         got[:, z0:z1] = u
     assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------- blocks in x, y and z
+def _run_block(rank, dims, bc, dist=None):
+    import torch
+
+    from oracle import stepper as st
+    from paper_2004_02833_gb300 import halo, synth
+
+    inst, u0 = synth.random_instance(N, SHAPE, seed=78, bc=bc)
+    H = halo.BlockHalo(N, SHAPE, dims, rank, bc == "periodic")
+    gx, gy, gz = (H.global_index(d) for d in range(3))
+    box = np.ix_(gz, gy, gx)
+    P = st.Problem(N, inst.sigma_a[box], inst.sigma_s[box], inst.q[box], inst.h, inst.dt, bc)
+    u = torch.tensor(u0[(slice(None),) + box])
+    own = H.own_slices()
+    outside = torch.ones(u.shape[1:], dtype=torch.bool)
+    outside[own] = False
+    for _ in range(STEPS):
+        for cls, tau in ((1, 0.5 * inst.dt), (0, inst.dt), (1, 0.5 * inst.dt)):
+            # everything outside the own block (faces, edges, corners) is NaN until the exchange
+            # fills the face layers a substep of class `cls` reads
+            u[:, outside] = float("nan")
+            H.exchange(u, cls, dist)
+            with np.errstate(invalid="ignore"):
+                u = torch.tensor(P.substep(u.numpy(), cls, tau))
+    lo = [H.lo_hi[d][0] for d in range(3)]
+    hi = [H.lo_hi[d][1] for d in range(3)]
+    return (lo[2], hi[2], lo[1], hi[1], lo[0], hi[0]), u.numpy()[(slice(None),) + own]
+
+
+def _block_worker(rank, dims, port, bc, q):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    world = dims[0] * dims[1] * dims[2]
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        q.put((rank,) + _run_block(rank, dims, bc, dist))
+    finally:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _block_reference(bc):
+    from oracle import stepper as st
+    from paper_2004_02833_gb300 import synth
+
+    inst, u0 = synth.random_instance(N, SHAPE, seed=78, bc=bc)
+    return st.Problem(N, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, bc).run(u0, STEPS)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "vacuum"])
+def test_one_block_equals_the_plain_run(bc):
+    box, u = _run_block(0, (1, 1, 1), bc)
+    assert box == (0, SHAPE[0], 0, SHAPE[1], 0, SHAPE[2])
+    assert np.array_equal(u, _block_reference(bc))
+
+
+@pytest.mark.parametrize("dims", [(2, 1, 1), (1, 2, 1), (2, 2, 1), (1, 2, 2)])
+@pytest.mark.parametrize("bc", ["periodic", "vacuum"])
+def test_gloo_blocks_equal_one_rank_bitwise(bc, dims):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    world = dims[0] * dims[1] * dims[2]
+    procs = [ctx.Process(target=_block_worker, args=(r, dims, port, bc, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=240) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    ref = _block_reference(bc)
+    got = np.full_like(ref, np.nan)
+    for _, (z0, z1, y0, y1, x0, x1), u in out:
+        got[:, z0:z1, y0:y1, x0:x1] = u
+    assert np.array_equal(got, ref)
