@@ -196,3 +196,17 @@ def test_gloo_blocks_equal_one_rank_bitwise(bc, dims):
     for _, (z0, z1, y0, y1, x0, x1), u in out:
         got[:, z0:z1, y0:y1, x0:x1] = u
     assert np.array_equal(got, ref)
+
+
+def test_block_faces_carry_a_quarter_of_the_moments_on_every_axis():
+    from paper_2004_02833_gb300 import halo
+
+    H = halo.BlockHalo(7, (8, 8, 8), (2, 2, 2), 0, True)
+    for A in (0, 1):
+        n_b = 28 if A == 1 else 36  # class B at N = 7: even l (28) for A = 1, odd l (36) for A = 0
+        for d in range(3):
+            up, lo = H.upper_sources[A][d], H.lower_sources[A][d]
+            assert not set(up) & set(lo) and len(up) + len(lo) == n_b
+            assert abs(len(up) - 16) <= 4 and abs(len(lo) - 16) <= 4
+    # neighbours of rank 0 in a periodic 2 x 2 x 2 grid: rank + 1 along x, + 2 along y, + 4 along z
+    assert H.upper == [1, 2, 4] and H.lower == [1, 2, 4]
