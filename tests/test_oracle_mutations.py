@@ -306,3 +306,25 @@ def test_planted_vacuum_mistake_is_caught(coupling_cache, monkeypatch):
     mats, slots = coupling_cache(3)
     monkeypatch.setattr(st, "shift", _shift_wraps_always)
     assert _vacuum_error(mats, slots) > 1e-6
+
+
+def _dE_closed_form_near_zero(x):
+    """E'(x) by the closed form down to |x| = 1e-3 (the cancellation the series avoids)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    small = np.abs(x) < 1e-3
+    xs = x[small]
+    out[small] = 0.5 + xs / 3.0 + xs**2 / 8.0 + xs**3 / 30.0 + xs**4 / 144.0
+    xl = x[~small]
+    out[~small] = (np.exp(xl) * (xl - 1.0) + 1.0) / (xl * xl)
+    return out
+
+
+def test_planted_inaccurate_dE_is_caught(monkeypatch):
+    # the extended-precision pin of E' (Eq. 5) catches the closed form evaluated near zero
+    from test_oracle_step import test_dE_matches_extended_precision
+
+    pytest.importorskip("mpmath")
+    monkeypatch.setattr(st, "_dE", _dE_closed_form_near_zero)
+    with pytest.raises(AssertionError):
+        test_dE_matches_extended_precision()
