@@ -235,8 +235,8 @@ int rtpn_count_nonfinite(rtpn_ctx* ctx, long long* out);
  * scratch is a file-scope device array of 2^16 FP64 partial sums (512 KB) that every GPU which
  * loads this library holds until the process exits, so n is limited to 2^30 values (RTPN_EINVAL
  * beyond, with the reason in rtpn_last_error(NULL)).  The sum is taken in a fixed order and is
- * reproducible.  The first call on a device looks up the scratch's device address, so make that
- * first call before any stream capture.  Every call shares the one scratch array and each call
+ * reproducible.  The first call on a device looks up the scratch's device address (again after a
+ * device reset gives the device a new context), so make that first call before any stream capture.  Every call shares the one scratch array and each call
  * overwrites the partials it reads (nothing has to start at zero); calls that overlap on the GPU
  * (on streams with no ordering between them) race and give wrong sums.  Asynchronous; RTPN_EINVAL
  * on NULL pointers, n < 0 or a bad dtype; RTPN_ECUDA if a launch fails.
@@ -260,6 +260,17 @@ int rtpn_sum_static(const void* x, int dtype, long long n, double* out, void* st
  */
 int rtpn_adjoint(rtpn_ctx* ctx, const void* w, int dtype, int where, int k, int ckpt_every,
                  double* g_sa, double* g_ss, double* g_q, int out_where, double* J);
+
+/*
+ * The detector functional that rtpn_adjoint differentiates, on the current state:
+ *     J = sum over cells of w * u_0
+ * accumulated in FP64 in a fixed order (1024 block partials, then one block; deterministic).  The
+ * paper defines no detector; this is the functional of the adjoint form.  w is [z][y][x] of dtype
+ * (RTPN_DTYPE_F64 / _F32) at `where`; J is one double at J_where (RTPN_HOST: synchronises;
+ * RTPN_DEVICE: ordered on the context's stream, nothing waits).  RTPN_EINVAL on NULL pointers or
+ * a bad dtype/where.
+ */
+int rtpn_detector(rtpn_ctx* ctx, const void* w, int dtype, int where, double* J, int J_where);
 
 /* ======================================================================== batched form
  * Many independent instances of uneven order N and grid size advanced together.  Each pass of the

@@ -46,10 +46,24 @@ __device__ __forceinline__ bool nb_cell(const Geom& g, int x, int y, int z, int 
     return true;
 }
 
-// E'(x) = (e^x (x - 1) + 1) / x^2; its Taylor series sum x^k (k+1)/(k+2)! near 0.
+// E'(x) for E(x) = expm1(x) / x of Eq. (5).  For |x| < 1 its Taylor polynomial
+// sum_{k<24} (k+1)/(k+2)! x^k by Horner's rule (coefficients built from the recurrence
+// c_k = c_{k-1} (k+1) / (k (k+2)), c_0 = 1/2; the tail is below 1e-23); for |x| >= 1 the form
+// (x e^x - expm1(x)) / x^2, whose numerator no longer cancels.  The closed form near 0 would lose
+// about eps / x^2 of its value (1e-10 at |x| = 1e-3).
 __device__ __forceinline__ double dE(double x) {
-    if (fabs(x) < 1e-3) return 0.5 + x / 3.0 + x * x / 8.0 + x * x * x / 30.0 + x * x * x * x / 144.0;
-    return (exp(x) * (x - 1.0) + 1.0) / (x * x);
+    if (fabs(x) < 1.0) {
+        constexpr int K = 24;
+        double c[K];
+        c[0] = 0.5;
+#pragma unroll
+        for (int k = 1; k < K; ++k) c[k] = c[k - 1] * (double)(k + 1) / ((double)k * (double)(k + 2));
+        double p = c[K - 1];
+#pragma unroll
+        for (int k = K - 2; k >= 0; --k) p = fma(p, x, c[k]);
+        return p;
+    }
+    return (x * exp(x) - expm1(x)) / (x * x);
 }
 
 // dalpha/dc and dbeta/dc per slot code for tau = dt (planes 0..15) and dt/2 (16..31), u_0 (32, 33)
@@ -250,6 +264,21 @@ __global__ void k_copy_cast(const A* __restrict__ in, B* __restrict__ out, long 
 
 unsigned blocks_for(long long V, int threads = 256) { return (unsigned)((V + threads - 1) / threads); }
 
+// out = sum of partial[0 .. count) in a fixed order (one block)
+__global__ void k_partials_total(const double* __restrict__ partial, int count, double* __restrict__ out) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) acc += partial[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += ws[i];
+        *out = s;
+    }
+}
+
 }  // namespace
 
 // Transposed partner table of class B targets (sources = class A, the w planes), host side.
@@ -391,13 +420,15 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
     cudaMemcpyAsync(fin.p, u, state, cudaMemcpyDeviceToDevice, st);
     // FP32 with the staged kernel: tensor maps over every pre-substep state slot of a segment
     Buf premaps;
+    size_t mapb = 0;
     bool staged_targets = false;
     if constexpr (sizeof(F) == 4 && sizeof(S) == 4) {
         if (ctx->active_kernel == RTPN_KERNEL_STAGE) {
-            if (!premaps.alloc((size_t)npass * 4 * 128)) return afail(ctx, RTPN_ENOMEM, "adjoint: tensor maps");
-            staged_targets = true;
+            mapb = stage_maps_bytes(ctx);
+            if (!premaps.alloc((size_t)npass * mapb)) return afail(ctx, RTPN_ENOMEM, "adjoint: tensor maps");
+            staged_targets = mapb > 0;
             for (int p = 0; p < npass && staged_targets; ++p)
-                staged_targets = stage_maps_for(ctx, (char*)seg.p + (size_t)p * state, (char*)premaps.p + (size_t)p * 512) == 0;
+                staged_targets = stage_maps_for(ctx, (char*)seg.p + (size_t)p * state, (char*)premaps.p + (size_t)p * mapb) == 0;
         }
     }
     for (int sg = nseg - 1; sg >= 0; --sg) {
@@ -413,7 +444,7 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
             const S* pre = (const S*)((char*)seg.p + (size_t)p * state);
             if (staged_targets) {
                 // the same pull-back on the staged kernel (column sweep over the pre-substep state)
-                const int rc2 = launch_stage_adjoint_targets(ctx, cls, ofs, (const char*)premaps.p + (size_t)p * 512,
+                const int rc2 = launch_stage_adjoint_targets(ctx, cls, ofs, (const char*)premaps.p + (size_t)p * mapb,
                                                              (float*)lam.p, (float*)wbuf.p, (const float*)dfac.p,
                                                              ctx->media + 2 * V, (double*)gacc.p, (double*)gqb.p, st);
                 if (rc2) return afail(ctx, RTPN_ECUDA, "adjoint: staged pull-back failed");
@@ -486,5 +517,43 @@ extern "C" int rtpn_adjoint(rtpn_ctx* ctx, const void* w, int dtype, int where, 
     for (int i = 0; i < 3; ++i) cudaMemcpyAsync(dst[i], o + (size_t)i * V, V * sizeof(double), kind, ctx->stream);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return afail(ctx, RTPN_ECUDA, cudaGetErrorString(e));
+    return RTPN_OK;
+}
+
+extern "C" int rtpn_detector(rtpn_ctx* ctx, const void* w, int dtype, int where, double* J, int J_where) {
+    if (!ctx || !w || !J) return RTPN_EINVAL;
+    if ((dtype != RTPN_DTYPE_F64 && dtype != RTPN_DTYPE_F32) || (where != RTPN_HOST && where != RTPN_DEVICE) ||
+        (J_where != RTPN_HOST && J_where != RTPN_DEVICE))
+        return afail(ctx, RTPN_EINVAL, "detector: bad dtype/where");
+    const long long V = ctx->g.V;
+    cudaStream_t st = ctx->stream;
+    // the weights as FP64 on the device: used in place, or widened into the context's FP64 staging plane
+    const double* wd = (const double*)w;
+    Buf tmp;
+    if (dtype == RTPN_DTYPE_F64 && where == RTPN_HOST) {
+        cudaMemcpyAsync(ctx->staging, w, (size_t)V * 8, cudaMemcpyHostToDevice, st);
+        wd = (const double*)ctx->staging;
+    } else if (dtype == RTPN_DTYPE_F32) {
+        const float* wf = (const float*)w;
+        if (where == RTPN_HOST) {
+            if (!tmp.alloc((size_t)V * 4)) return afail(ctx, RTPN_ENOMEM, "detector: weights");
+            cudaMemcpyAsync(tmp.p, w, (size_t)V * 4, cudaMemcpyHostToDevice, st);
+            wf = (const float*)tmp.p;
+        }
+        launch_convert<float, double>(wf, (double*)ctx->staging, V, st);
+        wd = (const double*)ctx->staging;
+    }
+    if (ctx->prec == RTPN_FP64)
+        k_dot_u0<double><<<SUM_BLOCKS, 256, 0, st>>>((const double*)ctx->u, wd, V, ctx->partial);
+    else if (ctx->prec == RTPN_FP32)
+        k_dot_u0<float><<<SUM_BLOCKS, 256, 0, st>>>((const float*)ctx->u, wd, V, ctx->partial);
+    else
+        k_dot_u0<__nv_bfloat16><<<SUM_BLOCKS, 256, 0, st>>>((const __nv_bfloat16*)ctx->u, wd, V, ctx->partial);
+    k_partials_total<<<1, 1024, 0, st>>>(ctx->partial, SUM_BLOCKS, ctx->partial + SUM_BLOCKS);
+    cudaError_t e = cudaMemcpyAsync(J, ctx->partial + SUM_BLOCKS, sizeof(double),
+                                    J_where == RTPN_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && (J_where == RTPN_HOST || tmp.p)) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return afail(ctx, RTPN_ECUDA, std::string("detector: ") + cudaGetErrorString(e));
     return RTPN_OK;
 }

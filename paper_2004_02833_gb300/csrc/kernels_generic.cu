@@ -107,11 +107,12 @@ template void launch_substep_generic<__nv_bfloat16, float>(__nv_bfloat16*, const
                                                            int, cudaStream_t);
 
 // ------------------------------------------------------------------ media -> substep factors
-// alpha = exp(-c tau), beta = tau E(-c tau) = -expm1(-c tau)/c (beta = tau at c = 0); FP64 library
-// exp/expm1, rounded to F on store.
+// alpha = exp(-c tau), beta = tau E(-c tau) = -expm1(-c tau)/c (beta = tau at c = 0), for any real c
+// (the same analytic expression on both sides of 0, so a derivative in sigma taken by differences
+// at sigma = 0 sees one smooth function); FP64 library exp/expm1, rounded to F on store.
 __device__ __forceinline__ void factors(double c, double tau, double* al, double* be) {
     *al = exp(-c * tau);
-    *be = c > 0.0 ? -expm1(-c * tau) / c : tau;
+    *be = c != 0.0 ? -expm1(-c * tau) / c : tau;
 }
 
 template <typename F>

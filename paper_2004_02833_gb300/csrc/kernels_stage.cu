@@ -14,7 +14,7 @@ namespace stg {
 #define RTPN_SDECL(n, x, y, z, b, e)                                                                 \
     int stage_launch_##n##_##x##_##y##_##z##_##b##_##e(int, int, int, const Args&, int, cudaStream_t);  \
     int stage_smem_##n##_##x##_##y##_##z##_##b##_##e(int, int);                                          \
-    int stage_boxcomps_##n##_##x##_##y##_##z##_##b##_##e(int);
+    void stage_geom_##n##_##x##_##y##_##z##_##b##_##e(int, int*);
 RTPN_STAGE_VARIANTS(RTPN_SDECL)
 #undef RTPN_SDECL
 
@@ -22,11 +22,11 @@ struct Variant {
     int N, tx, ty, tz, depth;
     int (*launch)(int, int, int, const Args&, int, cudaStream_t);  // (cls, precision, mode, ...)
     int (*smem)(int, int);
-    int (*boxcomps)(int);
+    void (*geom)(int, int*);  // (precision, {maps per kind, box length step, x group width, x group rows})
 };
 #define RTPN_SENTRY(n, x, y, z, b, e)                                                                \
     Variant{n, x, y, z, b, stage_launch_##n##_##x##_##y##_##z##_##b##_##e,                           \
-            stage_smem_##n##_##x##_##y##_##z##_##b##_##e, stage_boxcomps_##n##_##x##_##y##_##z##_##b##_##e},
+            stage_smem_##n##_##x##_##y##_##z##_##b##_##e, stage_geom_##n##_##x##_##y##_##z##_##b##_##e},
 static const Variant kVariants[] = {RTPN_STAGE_VARIANTS(RTPN_SENTRY)};
 #undef RTPN_SENTRY
 
@@ -71,7 +71,34 @@ static bool make_map(CUtensorMap* m, void* base, int precision, const rtpn::Geom
     return r == CUDA_SUCCESS;
 }
 
+// The tensor maps of one array for a variant (kinds MAP_PLANE, MAP_YROW, MAP_XGRP, each for box
+// lengths E = eq, 2 eq, ..., nmap eq; see stage_impl.cuh) into out[0 .. kinds * nmap); kinds = 1 builds
+// the plane maps only (target arrays).
+static bool make_maps(CUtensorMap* out, void* base, int precision, const rtpn::Geom& g, int nc, const Variant& v,
+                      int kinds) {
+    int geo[4];
+    v.geom(precision, geo);
+    const int nmap = geo[0], eq = geo[1], xw = geo[2], ry = geo[3];
+    for (int j = 0; j < nmap; ++j) {
+        const int e = eq * (j + 1);
+        if (!make_map(&out[MAP_PLANE * nmap + j], base, precision, g, nc, v.tx, v.ty, 1, e)) return false;
+        if (kinds > 1 && (!make_map(&out[MAP_YROW * nmap + j], base, precision, g, nc, v.tx, 1, v.tz, e) ||
+                          !make_map(&out[MAP_XGRP * nmap + j], base, precision, g, nc, xw, ry, v.tz, e)))
+            return false;
+    }
+    return true;
+}
+
+static int nmaps_of(const Variant& v, int precision) {
+    int geo[4];
+    v.geom(precision, geo);
+    return geo[0];
+}
+
 }  // namespace stg
+
+// device tensor-map slots of a context: forward (all kinds), adjoint w (all kinds), adjoint lam (plane)
+static constexpr int stage_maps_capacity = (2 * stg::MAP_KINDS + 1) * stg::kMaxSlots;
 
 bool stage_supported(int N, int precision, int nx) {
     if (precision == RTPN_FP64 || !stg::find(N, 0, 0, 0, 0, precision)) return false;
@@ -95,26 +122,21 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
                 break;
             }
     const int N = ctx->N;
-    const int es = ctx->prec == RTPN_BF16 ? 2 : 4;
-    const int hx = 16 / es;
-    // the four tensor maps live in device global memory (64-byte aligned) and the kernel reads
-    // them from there: tile box, x-halo group, y-halo row, z-halo plane, each spanning E consecutive
-    // components of a (type, |m|) run
-    const int e = v->boxcomps(ctx->prec);
-    if (e <= 0) return (int)cudaErrorInvalidValue;
-    alignas(64) CUtensorMap maps[4];
-    if (!stg::make_map(&maps[0], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, v->tz, e) ||
-        !stg::make_map(&maps[1], ctx->u, ctx->prec, ctx->g, ctx->md.nc, hx, v->ty, v->tz, e) ||
-        !stg::make_map(&maps[2], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, 1, v->tz, e) ||
-        !stg::make_map(&maps[3], ctx->u, ctx->prec, ctx->g, ctx->md.nc, v->tx, v->ty, 1, e))
+    // the tensor maps live in device global memory (64-byte aligned) and the kernel reads them from
+    // there: tile planes / z halo plane, y halo row and x halo group, each for every box length
+    const int nmap = stg::nmaps_of(*v, ctx->prec);
+    if (nmap <= 0 || nmap > stg::kMaxSlots) return (int)cudaErrorInvalidValue;
+    std::vector<CUtensorMap> maps((size_t)stg::MAP_KINDS * nmap);
+    if (!stg::make_maps(maps.data(), ctx->u, ctx->prec, ctx->g, ctx->md.nc, *v, stg::MAP_KINDS))
         return (int)cudaErrorInvalidValue;
     if (!ctx->stage_maps_dev) {
-        // the forward's four maps, then room for the adjoint's five
-        cudaError_t err = cudaMalloc(&ctx->stage_maps_dev, 9 * sizeof(CUtensorMap));
+        // the forward's maps, then room for the adjoint's (all kinds over w, plane maps over lam)
+        cudaError_t err = cudaMalloc(&ctx->stage_maps_dev, stage_maps_capacity * sizeof(CUtensorMap));
         if (err != cudaSuccess) return (int)err;
     }
     {
-        cudaError_t err = cudaMemcpy(ctx->stage_maps_dev, maps, sizeof(maps), cudaMemcpyHostToDevice);
+        cudaError_t err = cudaMemcpy(ctx->stage_maps_dev, maps.data(), maps.size() * sizeof(CUtensorMap),
+                                     cudaMemcpyHostToDevice);
         if (err != cudaSuccess) return (int)err;
         ctx->stage_adj_lam = ctx->stage_adj_w = nullptr;  // the adjoint's maps follow the tile
     }
@@ -229,19 +251,19 @@ int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long
     return v.launch(cls, ctx->prec, stg::FORWARD, a, ctx->sms, st);
 }
 
+size_t stage_maps_bytes(const rtpn_ctx* ctx) {
+    if (ctx->stage_variant < 0) return 0;
+    return (size_t)stg::MAP_KINDS * stg::nmaps_of(stg::kVariants[ctx->stage_variant], ctx->prec) *
+           sizeof(CUtensorMap);
+}
+
 int stage_maps_for(rtpn_ctx* ctx, const void* state, void* maps_dev) {
     if (ctx->stage_variant < 0 || ctx->prec != RTPN_FP32) return (int)cudaErrorNotSupported;
     const stg::Variant& v = stg::kVariants[ctx->stage_variant];
-    const int e = v.boxcomps(RTPN_FP32);
-    alignas(64) CUtensorMap maps[4];
-    void* b = const_cast<void*>(state);
-    const int nc = ctx->md.nc;
-    if (!stg::make_map(&maps[0], b, RTPN_FP32, ctx->g, nc, v.tx, v.ty, v.tz, e) ||
-        !stg::make_map(&maps[1], b, RTPN_FP32, ctx->g, nc, 4, v.ty, v.tz, e) ||
-        !stg::make_map(&maps[2], b, RTPN_FP32, ctx->g, nc, v.tx, 1, v.tz, e) ||
-        !stg::make_map(&maps[3], b, RTPN_FP32, ctx->g, nc, v.tx, v.ty, 1, e))
+    std::vector<CUtensorMap> maps((size_t)stg::MAP_KINDS * stg::nmaps_of(v, RTPN_FP32));
+    if (!stg::make_maps(maps.data(), const_cast<void*>(state), RTPN_FP32, ctx->g, ctx->md.nc, v, stg::MAP_KINDS))
         return (int)cudaErrorInvalidValue;
-    return (int)cudaMemcpy(maps_dev, maps, sizeof(maps), cudaMemcpyHostToDevice);
+    return (int)cudaMemcpy(maps_dev, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
 }
 
 int launch_stage_adjoint_targets(rtpn_ctx* ctx, int cls, int fac_ofs, const void* maps_dev, float* lam,
@@ -292,20 +314,16 @@ int launch_stage_adjoint_sources(rtpn_ctx* ctx, int tgt_cls, float* lam, const f
                                  cudaStream_t st) {
     if (ctx->stage_variant < 0 || ctx->prec != RTPN_FP32) return (int)cudaErrorNotSupported;
     const stg::Variant& v = stg::kVariants[ctx->stage_variant];
-    // tensor maps over w (the four source box kinds) and over lam (target tile boxes), rebuilt when
-    // the arrays change (once per adjoint call); they follow the forward maps at slots 4..8
-    CUtensorMap* dev = (CUtensorMap*)ctx->stage_maps_dev + 4;
+    // tensor maps over w (every source box kind) and over lam (target planes), rebuilt when the
+    // arrays change (once per adjoint call); they follow the forward maps
+    const int nmap = stg::nmaps_of(v, RTPN_FP32);
+    CUtensorMap* dev = (CUtensorMap*)ctx->stage_maps_dev + stg::MAP_KINDS * nmap;
     if (ctx->stage_adj_lam != lam || ctx->stage_adj_w != w) {
-        const int e = v.boxcomps(RTPN_FP32);
-        alignas(64) CUtensorMap maps[5];
-        void* wp = const_cast<float*>(w);
-        if (!stg::make_map(&maps[0], wp, RTPN_FP32, ctx->g, w_planes, v.tx, v.ty, v.tz, e) ||
-            !stg::make_map(&maps[1], wp, RTPN_FP32, ctx->g, w_planes, 4, v.ty, v.tz, e) ||
-            !stg::make_map(&maps[2], wp, RTPN_FP32, ctx->g, w_planes, v.tx, 1, v.tz, e) ||
-            !stg::make_map(&maps[3], wp, RTPN_FP32, ctx->g, w_planes, v.tx, v.ty, 1, e) ||
-            !stg::make_map(&maps[4], lam, RTPN_FP32, ctx->g, ctx->md.nc, v.tx, v.ty, v.tz, e))
+        std::vector<CUtensorMap> maps((size_t)(stg::MAP_KINDS + 1) * nmap);
+        if (!stg::make_maps(maps.data(), const_cast<float*>(w), RTPN_FP32, ctx->g, w_planes, v, stg::MAP_KINDS) ||
+            !stg::make_maps(maps.data() + stg::MAP_KINDS * nmap, lam, RTPN_FP32, ctx->g, ctx->md.nc, v, 1))
             return (int)cudaErrorInvalidValue;
-        cudaError_t err = cudaMemcpy(dev, maps, sizeof(maps), cudaMemcpyHostToDevice);
+        cudaError_t err = cudaMemcpy(dev, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
         if (err != cudaSuccess) return (int)err;
         ctx->stage_adj_lam = lam;
         ctx->stage_adj_w = w;
@@ -335,7 +353,7 @@ int launch_stage_adjoint_sources(rtpn_ctx* ctx, int tgt_cls, float* lam, const f
         a.kz = kz < 1 ? 1 : (kz > a.ntz ? a.ntz : kz);
     }
     a.maps = dev;
-    a.tmap = dev + 4;
+    a.tmap = dev + stg::MAP_KINDS * nmap;
     a.src_c0 = 0;  // w holds only the source class, in its local order
     a.nc = w_planes;
     a.status = ctx->status;

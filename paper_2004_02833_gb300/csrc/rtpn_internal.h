@@ -127,8 +127,9 @@ int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long
 // FP32 contexts with the staged kernel prepared; returns cudaError_t.
 int launch_stage_adjoint_sources(rtpn_ctx* ctx, int tgt_cls, float* lam, const float* w, int w_planes,
                                  cudaStream_t st);
-// Four tensor maps of the staged kernel over another FP32 state (an adjoint segment's pre-substep
-// state) into maps_dev (device, 4 CUtensorMap); returns cudaError_t.
+// The tensor maps of the staged kernel over another FP32 state (an adjoint segment's pre-substep
+// state) into maps_dev (device, stage_maps_bytes(ctx) bytes, 128-byte aligned); returns cudaError_t.
+size_t stage_maps_bytes(const rtpn_ctx* ctx);
 int stage_maps_for(rtpn_ctx* ctx, const void* state, void* maps_dev);
 // The pull-back of the multipliers through a substep on class cls from its pre-substep state (maps
 // from stage_maps_for): media gradients into gacc / gq, w of class cls, lam of class cls scaled.
@@ -171,8 +172,8 @@ struct rtpn_ctx {
     void* stage_mem = nullptr;       // staged kernels: coupling tables of both classes + column starts
     size_t stage_tab_bytes[2] = {0, 0};
     int stage_variant = -1, sms = 0;
-    void* stage_maps_dev = nullptr;  // CUtensorMap of the staged kernel (device global memory): 4 over u,
-                                     // then 5 for the adjoint (4 over its w, 1 over its lam)
+    void* stage_maps_dev = nullptr;  // CUtensorMap of the staged kernel (device global memory): those over
+                                     // u, then the adjoint's (over its w, then over its lam)
     const void* stage_adj_lam = nullptr;  // arrays the adjoint maps were built for
     const void* stage_adj_w = nullptr;
 };

@@ -1,7 +1,6 @@
 // One variant of the TMA-staged substep kernel: order RTPN_SN, CTA tile RTPN_STX x RTPN_STY x
-// RTPN_STZ, RTPN_SNB stage buffers, at least RTPN_SEM components per TMA box, both target classes,
-// FP32 and BF16 storage.  kernels_stage.cu
-// dispatches to it.
+// RTPN_STZ, RTPN_SNB stage buffers, TMA box lengths in multiples of RTPN_SEM components, both target
+// classes, FP32 and BF16 storage.  kernels_stage.cu dispatches to it.
 #include "stage_impl.cuh"
 
 #if !defined(RTPN_SN) || !defined(RTPN_STX) || !defined(RTPN_STY) || !defined(RTPN_STZ) || !defined(RTPN_SNB) || \
@@ -58,6 +57,23 @@ int launch_one(const Args& a, int sms, cudaStream_t st) {
     }
 }
 
+// dynamic shared memory of the variant, or 0 if it does not fit a CTA
+template <int A, typename S>
+constexpr int smem_of() {
+    using L = Layout<kN, A, S, kTX, kTY, kTZ, kNB, kEM>;
+    return L::FITS ? L::BYTES : 0;
+}
+// box geometry of the variant for a storage precision (the host builds its tensor maps with it):
+// out = {maps per kind, box length step, x halo group width, x halo group rows}
+template <typename S>
+void geom_of(int* out) {
+    using L = Layout<kN, 0, S, kTX, kTY, kTZ, kNB, kEM>;
+    out[0] = L::NMAP;
+    out[1] = kEM;
+    out[2] = L::XW;
+    out[3] = L::RY;
+}
+
 }  // namespace
 
 // mode FORWARD: FP32 or BF16 storage; modes ADJ_SOURCES, ADJ_TARGETS: FP32 (the adjoint)
@@ -76,16 +92,11 @@ int RTPN_SVARIANT(stage_launch)(int cls, int precision, int mode, const Args& a,
     return cls == 0 ? launch_one<0, float, FORWARD>(a, sms, st) : launch_one<1, float, FORWARD>(a, sms, st);
 }
 
-// dynamic shared memory of the variant, or 0 if it does not fit a CTA
-template <int A, typename S>
-constexpr int smem_of() {
-    using L = Layout<kN, A, S, kTX, kTY, kTZ, kNB, kEM>;
-    return L::FITS ? L::BYTES : 0;
-}
-// components per TMA box of the variant for a storage precision (the host builds its maps with it)
-int RTPN_SVARIANT(stage_boxcomps)(int precision) {
-    return precision == RTPN_BF16 ? Layout<kN, 0, __nv_bfloat16, kTX, kTY, kTZ, kNB, kEM>::E
-                                  : Layout<kN, 0, float, kTX, kTY, kTZ, kNB, kEM>::E;
+void RTPN_SVARIANT(stage_geom)(int precision, int* out) {
+    if (precision == RTPN_BF16)
+        geom_of<__nv_bfloat16>(out);
+    else
+        geom_of<float>(out);
 }
 
 int RTPN_SVARIANT(stage_smem)(int cls, int precision) {

@@ -13,18 +13,20 @@
 //  * The column sweep is a runtime loop whose body handles one column for every l slot; the three
 //    live target columns are register arrays that shift by one column per iteration, so the body
 //    is the same for every column and fits the instruction cache.
-//  * A producer warp moves each source column into shared memory with the Tensor Memory Accelerator
-//    (cp.async.bulk.tensor): per type and box kind, boxes of E consecutive components of the
-//    (type, |m|) run, as many as the column needs.  The TMA unit of an SM spends on the order of
-//    60 cycles per box plus a few per box row, so boxes are large (E components) and tiles wide
-//    in x (fewer, longer rows); one producer warp issues them.  A column stage holds, per source
-//    component, the tile box plus one halo slab on the side its partners read along each axis (x:
-//    an aligned 16-byte group, y: one row, z: one plane), and the column's coupling constants (a
-//    plain bulk copy).  Periodic halos use wrapped coordinates; vacuum halos use out-of-range
-//    coordinates, which the TMA unit fills with zeros.  The same stage carries the tile boxes of
-//    the target column it finishes (column i - 1 in stage i; a tile has N + 2 stages).  NB stage
-//    buffers form a ring with a full / empty mbarrier pair each, so up to NB - 1 stages are in
-//    flight while one is computed.
+//  * A producer warp moves each column into shared memory with the Tensor Memory Accelerator
+//    (cp.async.bulk.tensor): one box per (type, box kind) holding all E components of the
+//    (type, |m|) run at once (a tensor map per box length E), so a column stage costs about fifteen
+//    TMA operations.  Every box kind has the same volume per component, U = TY * TX elements:
+//    the tile as TZ plane boxes [E][1][TY][TX], the y halo row [E][TZ][1][TX], the z halo plane
+//    [E][1][TY][TX] and the x halo [E][TZ][RY][XW] (XW * RY = TX: an aligned group of XW columns
+//    around the neighbour the partners read, with RY >= TY rows).  So component q of every region
+//    sits at q * U elements and each thread reaches all its operands through a few base addresses
+//    fixed once per column plus compile-time offsets: no address arithmetic per slot.  Periodic
+//    halos use wrapped coordinates; vacuum halos use out-of-range coordinates, which the TMA unit
+//    fills with zeros.  The same stage carries the tile boxes of the target column it finishes
+//    (column i - 1 in stage i; a tile has N + 2 stages) and the column's coupling constants (a
+//    plain bulk copy).  NB stage buffers form a ring with a full / empty mbarrier pair each, so up
+//    to NB - 1 stages are in flight while one is computed.
 //
 // CTAs are persistent (one per SM) and walk tiles in z-chunked order (z fastest inside a chunk of kz
 // tile layers, then x, then y), so the CTAs at work at any time cover a compact block and read one
@@ -64,7 +66,7 @@ using win::static_for;
 constexpr int kMaxSlots = 24;
 // The same for chunks of kChunk slots: `switch (first / kChunk) { RTPN_CHUNK_CASES(f) }` runs f(c) for
 // chunks c = first / kChunk .. 11, so a compiler sees kChunk slots as one straight-line block.
-constexpr int kChunk = 2;  // measured: 2 beats 4 and 8 (P39 FP32 45.3 / 46.1 / 47.5 ms per step)
+constexpr int kChunk = 2;
 #define RTPN_CHUNK_CASES(f)                                                                        \
     RTPN_SLOT_CASE(f, 0) RTPN_SLOT_CASE(f, 1) RTPN_SLOT_CASE(f, 2) RTPN_SLOT_CASE(f, 3)             \
     RTPN_SLOT_CASE(f, 4) RTPN_SLOT_CASE(f, 5) RTPN_SLOT_CASE(f, 6) RTPN_SLOT_CASE(f, 7)             \
@@ -90,6 +92,13 @@ constexpr int CPAD = 12;
 // lam_A <- alpha_A lam_A.
 constexpr int FORWARD = 0, ADJ_SOURCES = 1, ADJ_TARGETS = 2;
 
+// Tensor maps of one array: kind k in {MAP_PLANE, MAP_YROW, MAP_XGRP} for every box length
+// E = EQ, 2 EQ, ..., NL (index k * nmaps + E / EQ - 1).
+constexpr int MAP_PLANE = 0;  // [E][1][TY][TX]: a tile plane or the z halo plane (also target boxes)
+constexpr int MAP_YROW = 1;   // [E][TZ][1][TX]: the y halo row
+constexpr int MAP_XGRP = 2;   // [E][TZ][RY][XW]: the x halo group
+constexpr int MAP_KINDS = 3;
+
 struct Args {
     void* tgt;              // target array (u for a forward pass, lam for ADJ_SOURCES)
     // ADJ_TARGETS only
@@ -109,8 +118,8 @@ struct Args {
     int ntx, nty, ntz;
     int kz;                 // tile layers per z chunk of the walk
     long long tiles;
-    const CUtensorMap* maps;  // four tensor maps over the source array: tile, x halo, y halo, z halo
-    const CUtensorMap* tmap;  // tile map over the target array
+    const CUtensorMap* maps;  // MAP_KINDS * nmaps tensor maps over the source array
+    const CUtensorMap* tmap;  // nmaps MAP_PLANE maps over the target array
     int src_c0;               // first component of the source class in the source array
     int nc;                   // components (bound of the 4th tensor coordinate)
     unsigned* status;       // device status word (STATUS_TIMEOUT on a wait that ran out)
@@ -120,76 +129,54 @@ struct Args {
 
 __host__ __device__ constexpr int pad128(int bytes) { return (bytes + 127) / 128 * 128; }
 
-// Components per TMA box along the component axis.  A box lands at a 128-byte aligned shared-memory
-// address, so E times the bytes of one component of every box kind (tile, x halo, y halo, z halo)
-// must be a multiple of 128; among such E in [emin, 8] the one that holds a run of N/2 + 1 in the
-// fewest slots, then in the fewest boxes, is taken (each box costs the TMA unit a fixed overhead,
-// so a variant may ask for larger boxes at the price of shared memory).
-__host__ __device__ constexpr int box_comps(int N, int tx, int ty, int tz, int es, int emin) {
-    const int nl0 = N / 2 + 1;
-    const int kinds[4] = {tx * ty * tz * es, (16 / es) * ty * tz * es, tx * tz * es, tx * ty * es};
-    int best = 0, best_slots = 1 << 30;
-    for (int e = 8; e >= emin; --e) {
-        bool ok = true;
-        for (int k = 0; k < 4; ++k) ok = ok && (e * kinds[k]) % 128 == 0;
-        const int slots = (nl0 + e - 1) / e * e;
-        if (ok && slots < best_slots) {
-            best = e;
-            best_slots = slots;
-        }
-    }
-    return best;  // 0: no aligned box exists for this tile
+// Width XW of the x halo box: the widest group of 16-byte aligned columns that divides TX and
+// leaves RY = TX / XW >= TY rows (so the box volume per component is TZ * TX = U when TY == TZ).
+__host__ __device__ constexpr int xhalo_width(int tx, int ty, int es) {
+    int best = 0;
+    for (int w = 16 / es; w <= tx; w += 16 / es)
+        if (tx % w == 0 && tx / w >= ty) best = w;
+    return best;
 }
-__host__ __device__ constexpr int run_slots(int N, int e) { return e > 0 ? (N / 2 + e) / e * e : 0; }
+// slots of a run in shared memory: the longest run N/2 + 1 rounded up to a multiple of eq
+__host__ __device__ constexpr int run_slots(int N, int eq) { return (N / 2 + 1 + eq - 1) / eq * eq; }
 
-template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EM = 1>
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ = 1>
 struct Layout {
     static constexpr int B = 1 - A;
     static constexpr int ES = (int)sizeof(S);
-    static constexpr int E = box_comps(N, TX, TY, TZ, ES, EM > N / 2 + 1 ? N / 2 + 1 : EM);  // per box
-    static constexpr int NL = run_slots(N, E);              // run slots per type in shared memory
-    static constexpr int NG = NL / E;                       // boxes per run, at most
-    static constexpr int NLC = N / 2 + 1;                   // coupling-constant slots per type
-    static constexpr int HX = 16 / ES;    // x halo: one aligned 16-byte group
+    static constexpr int G = 16 / ES;                 // elements of an aligned 16-byte group
+    static constexpr int NL = run_slots(N, EQ);       // run slots per region
+    static constexpr int NMAP = NL / EQ;              // box lengths (tensor maps) per kind
+    static constexpr int NLC = N / 2 + 1;             // coupling-constant slots per type
+    static constexpr int U = TY * TX;                 // elements of one component in every box
+    static constexpr int UB = U * ES;
+    static constexpr int XW = xhalo_width(TX, TY, ES);
+    static constexpr int RY = XW > 0 ? TX / XW : 1;
     static constexpr int CELLS = TX * TY * TZ;
     static constexpr int CONSUMER_WARPS = 2 * CELLS / 32;
-    static constexpr int THREADS = 2 * CELLS + 32;          // two threads per cell + the producer
-    // bytes of one component in each box kind
-    static constexpr int CTR_BYTES = TX * TY * TZ * ES;
-    static constexpr int HX_BYTES = HX * TY * TZ * ES;
-    static constexpr int HY_BYTES = TX * TZ * ES;
-    static constexpr int HZ_BYTES = TX * TY * ES;
-    static constexpr int COMP_BYTES = CTR_BYTES + HX_BYTES + HY_BYTES + HZ_BYTES;
-    // regions of one type: the run's tile boxes, then its x, y and z halos
-    static constexpr int R_CTR = pad128(NL * CTR_BYTES);
-    static constexpr int R_HX = pad128(NL * HX_BYTES);
-    static constexpr int R_HY = pad128(NL * HY_BYTES);
-    static constexpr int R_HZ = pad128(NL * HZ_BYTES);
-    static constexpr int SRC_T = R_CTR + R_HX + R_HY + R_HZ;
-    static constexpr int HXO = R_CTR, HYO = R_CTR + R_HX, HZO = R_CTR + R_HX + R_HY;
-    static constexpr int COEF_COL = 2 * NLC * CPAD * 4;     // one column's coupling constants
-    static constexpr int R_TGT = pad128(NL * CTR_BYTES);     // tile boxes of one type's targets
-    // buffer layout: target boxes, type-0 sources, type-1 sources, coupling constants.  A chunked
-    // sweep reads up to kChunk - 1 slots (plus one neighbour offset) below a source region; with the
-    // targets first, such reads stay on state data (or the zeros the ring starts with) in the same
-    // buffer, never on the coupling constants, whose bits need not be finite in the storage type.
+    static constexpr int THREADS = 2 * CELLS + 32;   // two threads per cell + the producer
+    static constexpr int REG = pad128(NL * UB);       // one region: NL components of one box kind
+    // regions of one type's sources: TZ tile planes, then the y halo, z halo and x halo
+    static constexpr int KY = TZ, KZ = TZ + 1, KX = TZ + 2, NKIND = TZ + 3;
+    static constexpr int SRC_T = NKIND * REG;
+    static constexpr int TGT_T = TZ * REG;            // tile planes of one type's targets
+    static constexpr int COEF_COL = 2 * NLC * CPAD * 4;  // one column's coupling constants
+    // buffer layout: target planes, type-0 sources, type-1 sources, coupling constants.  A chunked
+    // sweep reads up to kChunk - 1 slots below a source region; with the targets first, such reads
+    // stay on state data (or the zeros the ring starts with) in the same buffer, never on the
+    // coupling constants, whose bits need not be finite in the storage type.
     static constexpr int TGTO = 0;
-    static constexpr int SRCO = 2 * R_TGT;
+    static constexpr int SRCO = 2 * TGT_T;
     static constexpr int COEFO = SRCO + 2 * SRC_T;
-    static constexpr int BUF = COEFO + pad128(COEF_COL);     // one stage buffer
+    static constexpr int BUF = COEFO + pad128(COEF_COL);  // one stage buffer
     static constexpr int BARS = pad128(2 * NB * 8);
-    static constexpr int BYTES = NB * BUF + BARS + 128;      // ring, mbarriers, base alignment slack
-    static_assert(2 * R_TGT >= (kChunk - 1) * CTR_BYTES + TX * TY * ES,
-                  "the target region must cover what a chunked sweep reads below the sources");
-    static_assert(TX % HX == 0, "tile width must be a multiple of the 16-byte group");
+    static constexpr int BYTES = NB * BUF + BARS + 128;   // ring, mbarriers, base alignment slack
+    static_assert(TY == TZ, "every box kind has the volume TY * TX per component only if TY == TZ");
+    static_assert(XW > 0, "no 16-byte x halo group divides the tile width");
+    static_assert(TX % G == 0, "tile width must be a multiple of the 16-byte group");
     static_assert(CELLS % 32 == 0, "a type's threads must fill whole warps");
-    static_assert(CTR_BYTES % 16 == 0 && HX_BYTES % 16 == 0 && HY_BYTES % 16 == 0 && HZ_BYTES % 16 == 0,
-                  "box components must stay 16-byte aligned");
     static_assert(NB >= 2 && NB <= 8, "two to eight stage buffers");
-    static_assert(E > 0, "no 128-byte aligned box for this tile");
-    static_assert((E * CTR_BYTES) % 128 == 0 && (E * HX_BYTES) % 128 == 0 && (E * HY_BYTES) % 128 == 0 &&
-                      (E * HZ_BYTES) % 128 == 0 && BUF % 128 == 0,
-                  "every box must land on a 128-byte boundary");
+    static_assert(REG >= (kChunk - 1) * UB, "a region must cover what a chunked sweep reads below the next");
     static constexpr bool FITS = BYTES <= 232448;  // 227 KB of shared memory per CTA
 };
 
@@ -269,7 +256,8 @@ __device__ __forceinline__ bool scheck_fail(unsigned* st, unsigned id, unsigned 
 #endif
 #define RTPN_SCHECK(cond) RTPN_SCHECK_ID(cond, __LINE__, 0)
 
-// Tile geometry: origin, valid extents and halo coordinates ([axis][side], side 1 = upper).
+// Tile geometry: origin, valid extents, halo coordinates ([axis][side], side 1 = upper) and, per
+// side, the origin of the x halo group box and the element of the neighbour column inside it.
 struct TileGeo {
     int x0, y0, z0, wx, wy, wz;
     int hc[3][2];
@@ -297,8 +285,9 @@ __host__ __device__ __forceinline__ void tile_coords(unsigned t, int ntx, int nt
     *by = (int)(rest / ntx);
 }
 
-template <int TX, int TY, int TZ, int HX>
-__device__ __forceinline__ TileGeo tile_geo(const Args& a, unsigned t) {
+// G: elements of a 16-byte group (the x halo box starts on one)
+template <int TX, int TY, int TZ, int G>
+__host__ __device__ __forceinline__ TileGeo tile_geo(const Args& a, unsigned t) {
     TileGeo g;
     int bx, by, bz;
     tile_coords(t, a.ntx, a.nty, a.ntz, a.kz, &bx, &by, &bz);
@@ -320,10 +309,11 @@ __device__ __forceinline__ TileGeo tile_geo(const Args& a, unsigned t) {
         g.hc[d][1] = up;
         g.hc[d][0] = lo;
     }
+    // the neighbour column xn sits at element xn - start of a box that starts on the group holding it
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         const int xn = g.hc[0][s];
-        const int st = xn >= 0 ? (xn / HX) * HX : -HX;
+        const int st = xn >= 0 ? (xn / G) * G : -G;
         g.hx_start[s] = st;
         g.hx_elem[s] = xn - st;
     }
@@ -331,16 +321,18 @@ __device__ __forceinline__ TileGeo tile_geo(const Args& a, unsigned t) {
 }
 
 // Source x slot: 1 (read at i+1 by its partners) iff (M even) == (cos type); z slot: 1 iff l+M even.
-__device__ __forceinline__ int dir_x(int M, int t) { return ((M & 1) == 0) == (t == 0) ? 1 : -1; }
+__host__ __device__ __forceinline__ int dir_x(int M, int t) { return ((M & 1) == 0) == (t == 0) ? 1 : -1; }
 
 // The producer warp: issues the copies of every stage of this CTA's sequence into the ring.
-template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EM>
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ>
 __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* bufs, unsigned full0,
                                                unsigned empty0, int total) {
-    using L = Layout<N, A, S, TX, TY, TZ, NB, EM>;
+    using L = Layout<N, A, S, TX, TY, TZ, NB, EQ>;
     constexpr int B = 1 - A;
     constexpr int NST = N + 2;
-    constexpr int E = L::E, NG = L::NG;
+    constexpr int NK = L::NKIND;
+    constexpr int NJOB = 2 * NK + 2 * TZ;  // source boxes (type, kind), then target planes (type, z)
+    static_assert(NJOB <= 32, "one box per lane");
     const int lane = threadIdx.x & 31;
     const int cA0 = A == 0 ? 0 : class_size(N, 0);
     const int cB0 = a.src_c0;
@@ -349,21 +341,21 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
     // advanced column by column (no table loads on the producer's path)
     int offB = 0, offA = 0;
     // the maps were written by the host before the launch; make them visible to the async proxy
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < MAP_KINDS * L::NMAP; ++k)
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + k) : "memory");
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(a.tmap) : "memory");
+    for (int k = 0; k < L::NMAP; ++k)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(a.tmap + k) : "memory");
 
     int s = 0;
     bool failed = false;
     int b = 0, i = 0;
     unsigned ph = 0;  // phase parity of buffer b's current use (flips when b wraps)
     unsigned tile = blockIdx.x;
-    TileGeo g = tile_geo<TX, TY, TZ, L::HX>(a, tile);
+    TileGeo g = tile_geo<TX, TY, TZ, L::G>(a, tile);
     for (; s < total; ++s, i = (i == NST - 1) ? 0 : i + 1) {
         if (i == 0 && s > 0) {
             tile += gridDim.x;
-            g = tile_geo<TX, TY, TZ, L::HX>(a, tile);
+            g = tile_geo<TX, TY, TZ, L::G>(a, tile);
             offB = offA = 0;
         }
         const unsigned full = full0 + 8 * b;
@@ -387,43 +379,46 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
         unsigned char* buf = bufs + bcur * L::BUF;
         const int len = column_len(N, i, B);     // sources of column i (none at i = N + 1)
         const int nt = len > 0 ? ntypes(i) : 0;  // source types present in the column
-        const int nbox = (len + E - 1) / E;
+        const int ebox = (len + EQ - 1) / EQ * EQ;
         const int M = i - 1;                     // target column finished in this stage
         const int lenA = M >= 0 ? column_len(N, M, A) : 0;
         const int ntA = lenA > 0 ? ntypes(M) : 0;
-        const int nboxA = (lenA + E - 1) / E;
-        const unsigned bytes = nt * nbox * E * L::COMP_BYTES + ntA * nboxA * E * L::CTR_BYTES +
-                               (nt > 0 ? L::COEF_COL : 0);
+        const int eboxA = (lenA + EQ - 1) / EQ * EQ;
+        const unsigned bytes = (unsigned)((nt * NK * ebox + ntA * TZ * eboxA) * L::UB) +
+                               (nt > 0 ? (unsigned)L::COEF_COL : 0u);
         if (lane == 0) mbar_expect_tx(full, bytes);
         __syncwarp();
-        // lane j < 8 NG: source box (type j / (4 NG), kind (j / NG) % 4, box j % NG);
-        // 8 NG <= j < 10 NG: target box (type (j - 8 NG) / NG, box j % NG)
-        for (int j = lane; j < 10 * NG; j += 32) {
-            if (j >= 8 * NG) {
-                const int t = (j - 8 * NG) / NG, k = j % NG;
-                if (t >= ntA || k >= nboxA) continue;
-                const int c = cA0 + offA_s + t * lenA + k * E;
-                if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 111, c)) continue;
-                tma_load_4d(smem_addr(buf + L::TGTO + t * L::R_TGT) + k * E * L::CTR_BYTES, a.tmap, g.x0, g.y0,
-                            g.z0, c, full);
-                continue;
-            }
-            const int t = j / (4 * NG), kind = (j / NG) % 4, k = j % NG;
-            if (t >= nt || k >= nbox) continue;
-            const int c = cB0 + offB_s + t * len + k * E;  // first component of the box
-            const unsigned d = smem_addr(buf + L::SRCO + t * L::SRC_T);
-            if (!RTPN_SCHECK_ID(c >= 0 && c < a.nc, 101, c)) continue;
-            if (kind == 0) {
-                tma_load_4d(d + k * E * L::CTR_BYTES, maps, g.x0, g.y0, g.z0, c, full);
-            } else if (kind == 1) {  // x slot 1 -> partners read i+1 (upper halo)
-                const int hxs = dir_x(i, t) > 0 ? g.hx_start[1] : g.hx_start[0];
-                tma_load_4d(d + L::HXO + k * E * L::HX_BYTES, maps + 1, hxs, g.y0, g.z0, c, full);
-            } else if (kind == 2) {  // cos type reads y+1, sin type y-1
-                tma_load_4d(d + L::HYO + k * E * L::HY_BYTES, maps + 2, g.x0, t == 0 ? g.hc[1][1] : g.hc[1][0],
-                            g.z0, c, full);
-            } else {                 // z slot 1 (l + M even) reads z+1
-                tma_load_4d(d + L::HZO + k * E * L::HZ_BYTES, maps + 3, g.x0, g.y0,
-                            ((B + i) & 1) == 0 ? g.hc[2][1] : g.hc[2][0], c, full);
+        if (lane < NJOB) {
+            const int j = lane;
+            if (j >= 2 * NK) {  // target plane lz of type t
+                const int t = (j - 2 * NK) / TZ, lz = (j - 2 * NK) % TZ;
+                if (t < ntA) {
+                    const int c = cA0 + offA_s + t * lenA;
+                    if (RTPN_SCHECK_ID(c >= 0 && c < a.nc && eboxA <= L::NL, 111, c))
+                        tma_load_4d(smem_addr(buf + L::TGTO + t * L::TGT_T + lz * L::REG), a.tmap + (eboxA / EQ - 1),
+                                    g.x0, g.y0, g.z0 + lz, c, full);
+                }
+            } else {
+                const int t = j / NK, k = j % NK;
+                if (t < nt) {
+                    const int c = cB0 + offB_s + t * len;  // first component of the run
+                    const unsigned d = smem_addr(buf + L::SRCO + t * L::SRC_T + k * L::REG);
+                    const CUtensorMap* mp = maps + (ebox / EQ - 1);
+                    if (RTPN_SCHECK_ID(c >= 0 && c < a.nc && ebox <= L::NL, 101, c)) {
+                        if (k < TZ) {               // tile plane z0 + k
+                            tma_load_4d(d, mp + MAP_PLANE * L::NMAP, g.x0, g.y0, g.z0 + k, c, full);
+                        } else if (k == L::KY) {    // cos-type sources are read at y+1, sin-type at y-1
+                            tma_load_4d(d, mp + MAP_YROW * L::NMAP, g.x0, t == 0 ? g.hc[1][1] : g.hc[1][0], g.z0, c,
+                                        full);
+                        } else if (k == L::KZ) {    // z slot 1 (l + M even) is read at z+1
+                            tma_load_4d(d, mp + MAP_PLANE * L::NMAP, g.x0, g.y0,
+                                        ((B + i) & 1) == 0 ? g.hc[2][1] : g.hc[2][0], c, full);
+                        } else {                    // x slot 1 is read at x+1 (upper halo group)
+                            tma_load_4d(d, mp + MAP_XGRP * L::NMAP, dir_x(i, t) > 0 ? g.hx_start[1] : g.hx_start[0],
+                                        g.y0, g.z0, c, full);
+                        }
+                    }
+                }
             }
         }
         if (lane == 0 && nt > 0)
@@ -437,19 +432,19 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
         if (r != a.skip_stage) wait_phase(full0 + 8 * (r % NB), (unsigned)((r / NB) & 1), a.wait_limit);
 }
 
-template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EM, int MODE>
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ, int MODE>
 __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* smem) {
-    using L = Layout<N, A, S, TX, TY, TZ, NB, EM>;
+    using L = Layout<N, A, S, TX, TY, TZ, NB, EQ>;
     static_assert(N >= 1, "order N >= 1");
     static_assert((N + 2) / 2 <= kMaxSlots, "slot switch covers N <= 45");
     constexpr int B = 1 - A;
     constexpr int NLA = (N - A) / 2 + 1;   // class-A components of a run, at most
     constexpr int NLB = (N - B) / 2 + 1;   // class-B components of a run, at most
     constexpr int CELLS = L::CELLS;
-    constexpr int HX = L::HX;
+    constexpr int UB = L::UB, REG = L::REG, ES = L::ES;
     constexpr int NST = N + 2;  // stage i: sources of column i (i <= N), targets of column i - 1
     const int cA0 = A == 0 ? 0 : class_size(N, 0);
-    const int* colA = a.colstart + A * (N + 2);
+    [[maybe_unused]] const int* colA = a.colstart + A * (N + 2);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const long long V = a.V;
@@ -477,47 +472,75 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     const int my_tiles = a.tiles > blockIdx.x ? (int)((a.tiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
     const int total = my_tiles * NST;
     if (warp == L::CONSUMER_WARPS) {
-        stage_producer<N, A, S, TX, TY, TZ, NB, EM>(a, bufs, full0, empty0, total);
+        stage_producer<N, A, S, TX, TY, TZ, NB, EQ>(a, bufs, full0, empty0, total);
         return;
     }
 
-    // ---- consumers: thread (T, cell) finishes the targets of type T in its cell
+    // ---- consumers: thread (T, cell) finishes the targets of type T in its cell.  Both types run
+    // the same code: the type only selects regions, coupling-constant rows and the y direction.
     const int T = tid / CELLS, ctid = tid % CELLS;
     const int lx = ctid % TX, ly = (ctid / TX) % TY, lz = ctid / (TX * TY);
-    const int my = ((lz * TY + ly) * TX + lx) * L::ES;
+    const int cp = (ly * TX + lx) * ES;  // the cell in a tile plane region (per component)
+    const int rbo = L::SRCO + T * L::SRC_T;         // own-type sources (z and x partners)
+    const int roo = L::SRCO + (1 - T) * L::SRC_T;   // other-type sources (y partners)
+    const int dy = T == 0 ? -1 : 1;                 // cos-type sources are read at y+1, sin-type at y-1
+    const int cown = T * L::NLC * CPAD, coth = (1 - T) * L::NLC * CPAD;  // coupling-constant rows (floats)
+    const int tgo = L::TGTO + T * L::TGT_T + lz * REG + cp;              // this cell's old target values
 
-    float prev[NLA], cur[NLA], next[NLA];
-#pragma unroll
-    for (int q = 0; q < NLA; ++q) prev[q] = cur[q] = next[q] = 0.f;
+    // the three live target columns; their roles (prev, cur, next) rotate by one per stage
+    float wa[NLA], wb[NLA], wc[NLA];
 
     TileGeo g{};
     bool active = false;
     long long cell = 0;
+    // byte offsets in a stage buffer, fixed per tile: the own source, the other type's source and
+    // its y partner, and per parity p of the source column the x and z partners
+    int off_c = 0, off_o = 0, off_y = 0, off_x0 = 0, off_x1 = 0, off_z0 = 0, off_z1 = 0;
     float alE = 0.f, beE = 0.f, alO = 0.f, beO = 0.f;  // Eq. (5) factors of columns M even / odd
     float al0 = 0.f, be0 = 0.f, ga0 = 0.f;             // u_0 (class 0, type 0 only)
     // ADJ_TARGETS: factor derivatives, the u_0 source, the multipliers of the target column being
     // finished (prefetched at the top of the stage) and this tile's media-gradient sums
     float daE = 0.f, dbE = 0.f, daO = 0.f, dbO = 0.f, da0 = 0.f, db0 = 0.f, q0s = 0.f;
     float lpre[MODE == ADJ_TARGETS ? NLA : 1];
+#pragma unroll
+    for (int q = 0; q < (MODE == ADJ_TARGETS ? NLA : 1); ++q) lpre[q] = 0.f;
     float gE = 0.f, gO = 0.f, g0 = 0.f, gqa = 0.f;
 
     // first local index of target column M in class A, advanced column by column (offA = colstart
-    // of the column finished next); component q = 0 of the run (type T, column M) at this cell
+    // of the column finished next)
     int offA = 0;
-    auto tgt_ptr = [&](int M) {
-        return reinterpret_cast<S*>(a.tgt) +
-               (long long)(cA0 + offA + T * column_len(N, M, A) - first_l(M, A) / 2) * V + cell;
-    };
-
     unsigned tile = blockIdx.x;
     int b = 0;
     unsigned ph = 0;
-    for (int s = 0, i = 0; s < total; ++s, i = (i == NST - 1) ? 0 : i + 1) {
-        if (i == 0) {  // new tile: geometry, factors
+    int s = 0, i = 0;
+
+    // One stage: sweep source column i into prev (column i - 1), cur (i) and next (i + 1), finish
+    // prev, and clear it (it is the next stage's `next`).  False if a wait ran out.
+    auto stage = [&](float (&prev)[NLA], float (&cur)[NLA], float (&next)[NLA]) -> bool {
+        if (i == 0) {  // new tile: geometry, operand offsets, factors, a cleared window
             if (s > 0) tile += gridDim.x;
-            g = tile_geo<TX, TY, TZ, HX>(a, tile);
+            g = tile_geo<TX, TY, TZ, L::G>(a, tile);
             active = lx < g.wx && ly < g.wy && lz < g.wz;
             cell = ((long long)(g.z0 + lz) * a.ny + (g.y0 + ly)) * a.nx + (g.x0 + lx);
+            off_c = rbo + lz * REG + cp;
+            off_o = roo + lz * REG + cp;
+            off_y = (ly + dy >= 0 && ly + dy < g.wy) ? off_o + dy * TX * ES : roo + L::KY * REG + (lz * TX + lx) * ES;
+            auto xoff = [&](int p) {
+                const int dx = dir_x(p, T);
+                return (lx + dx >= 0 && lx + dx < g.wx)
+                           ? off_c + dx * ES
+                           : rbo + L::KX * REG + ((lz * L::RY + ly) * L::XW + (dx > 0 ? g.hx_elem[1] : g.hx_elem[0])) * ES;
+            };
+            auto zoff = [&](int p) {
+                const int dz = ((B + p) & 1) == 0 ? 1 : -1;
+                return (lz + dz >= 0 && lz + dz < g.wz) ? off_c + dz * REG : rbo + L::KZ * REG + cp;
+            };
+            off_x0 = xoff(0);
+            off_x1 = xoff(1);
+            off_z0 = zoff(0);
+            off_z1 = zoff(1);
+#pragma unroll
+            for (int q = 0; q < NLA; ++q) prev[q] = cur[q] = next[q] = 0.f;
             if (MODE != ADJ_SOURCES && active) {  // the transposed coupling uses no factors
                 // sub-grid slot of (l, M, T) in class A: x by (M, T), y by T, z by (A + M)
 #pragma unroll
@@ -560,7 +583,11 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                 }
             }
         }
-        const bool fin = active && i >= 1 && (T == 0 || i - 1 >= 1);  // target column i - 1 of type T
+        // target column i - 1 of type T is finished in this stage (the same for the whole warp); the
+        // sweep and the finish run on every thread of the tile (a thread past the grid's edge works
+        // on zero-filled or in-tile shared memory), only global memory accesses need an active cell
+        const bool finw = i >= 1 && (T == 0 || i - 1 >= 1);
+        const bool fin = active && finw;
         if constexpr (MODE == ADJ_TARGETS) {
             if (fin) {  // the multipliers of column i - 1, for the finish below
                 const int M = i - 1, q0 = first_l(M, A) / 2;
@@ -573,117 +600,85 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
 
         if (!__all_sync(0xffffffffu, wait_phase(full0 + 8 * b, ph, a.wait_limit))) {
             if (lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
-            break;
+            return false;
         }
         const unsigned char* buf = bufs + b * L::BUF;
 
-        if (active && column_len(N, i, B) > 0) {
-            // ---- scatter source column i into prev (i-1), cur (i), next (i+1)
-            const int Ms = i;
-            const int fq = first_l(Ms, B) / 2;  // run slot of source q is q - fq
+        if (column_len(N, i, B) > 0) {
+            // ---- scatter source column i into prev (i-1), cur (i), next (i+1).  At |m| = 0 only the
+            // cos type exists: the absent type's constants are zero (its regions hold earlier, finite
+            // data), so the same sweep serves every column.
+            const int fq = first_l(i, B) / 2;  // run slot of source q is q - fq
+            const int sh = -fq * UB;           // so source q sits at q * UB from each base
+            const unsigned char* pc = buf + off_c + sh;
+            const unsigned char* px = buf + ((i & 1) ? off_x1 : off_x0) + sh;
+            const unsigned char* pz = buf + ((i & 1) ? off_z1 : off_z0) + sh;
+            const unsigned char* po = buf + off_o + sh;
+            const unsigned char* py = buf + off_y + sh;
             const float* cf = reinterpret_cast<const float*>(buf + L::COEFO);
-            static_for<2>([&](auto Ti) {
-                constexpr int TT = decltype(Ti)::value;
-                if (T != TT) return;
-                constexpr int O = 1 - TT;                  // the other type
-                const int dz = ((B + Ms) & 1) == 0 ? 1 : -1;
-                // a tile one cell thick along an axis always reads that axis' partner from the halo
-                const bool inz = TZ > 1 && lz + dz >= 0 && lz + dz < g.wz;
-                const int dx = dir_x(Ms, TT);
-                const bool inx = lx + dx >= 0 && lx + dx < g.wx;
-                constexpr int dy = O == 0 ? 1 : -1;        // the other type's y partner
-                const bool iny = TY > 1 && ly + dy >= 0 && ly + dy < g.wy;
-                const unsigned char* rb = buf + L::SRCO + TT * L::SRC_T;
-                const unsigned char* ro = buf + L::SRCO + O * L::SRC_T;
-                // per neighbour: address of run slot -fq (so source q sits at q) and the slot stride
-                const unsigned char* pc = rb + my - fq * L::CTR_BYTES;
-                const unsigned char* px =
-                    inx ? pc + dx * L::ES
-                        : rb + L::HXO + ((lz * TY + ly) * HX + (dx > 0 ? g.hx_elem[1] : g.hx_elem[0])) * L::ES -
-                              fq * L::HX_BYTES;
-                const int sx = inx ? L::CTR_BYTES : L::HX_BYTES;
-                const unsigned char* pz =
-                    inz ? pc + dz * TX * TY * L::ES : rb + L::HZO + (ly * TX + lx) * L::ES - fq * L::HZ_BYTES;
-                const int sz = inz ? L::CTR_BYTES : L::HZ_BYTES;
-                const unsigned char* po = ro + my - fq * L::CTR_BYTES;
-                const unsigned char* py =
-                    iny ? po + dy * TX * L::ES : ro + L::HYO + (lz * TX + lx) * L::ES - fq * L::HY_BYTES;
-                const int sy = iny ? L::CTR_BYTES : L::HY_BYTES;
-                const float4* cown = reinterpret_cast<const float4*>(cf + TT * L::NLC * CPAD);
-                const float4* coth = reinterpret_cast<const float4*>(cf + O * L::NLC * CPAD);
-                // sources q = fq .. NLB - 1 (q < fq has l < Ms: not in the column)
-                auto sweep = [&](auto own_c, auto oth_c) {
-                    constexpr bool OWN = decltype(own_c)::value, OTH = decltype(oth_c)::value;
-                    auto slot = [&](auto qi) {
-                        constexpr int q = decltype(qi)::value;
-                        if constexpr (q < NLB) {
-                            constexpr int ls = 2 * q + B;
-                            constexpr int lm = (ls - 1) / 2, lp = (ls + 1) / 2;  // acc index of l-1, l+1
-                            constexpr bool has_m = ls - 1 >= 0 && lm < NLA;
-                            constexpr bool has_p = ls + 1 <= N && lp < NLA;
-                            if constexpr (has_m || has_p) {
-                                if (!RTPN_SCHECK(q - fq >= -(kChunk - 1) && q - fq < column_len(N, Ms, B))) return;
-                                constexpr int am = has_m ? lm : 0, ap = has_p ? lp : 0;
-                                if constexpr (OWN) {
-                                    const float c = lds<S>(pc, q * L::CTR_BYTES);
-                                    const float ddx = lds<S>(px, q * sx) - c;
-                                    const float ddz = lds<S>(pz, q * sz) - c;
-                                    const float4 k0 = cown[3 * q], k1 = cown[3 * q + 1];
-                                    if constexpr (has_m) cur[am] = fmaf(k0.x, ddz, cur[am]);
-                                    if constexpr (has_p) cur[ap] = fmaf(k0.y, ddz, cur[ap]);
-                                    if constexpr (has_m) prev[am] = fmaf(k0.z, ddx, prev[am]);
-                                    if constexpr (has_p) prev[ap] = fmaf(k0.w, ddx, prev[ap]);
-                                    if constexpr (has_m) next[am] = fmaf(k1.x, ddx, next[am]);
-                                    if constexpr (has_p) next[ap] = fmaf(k1.y, ddx, next[ap]);
-                                }
-                                if constexpr (OTH) {
-                                    const float c = lds<S>(po, q * L::CTR_BYTES);
-                                    const float ddy = lds<S>(py, q * sy) - c;
-                                    const float4 k2 = coth[3 * q + 2];
-                                    if constexpr (has_m) prev[am] = fmaf(k2.x, ddy, prev[am]);
-                                    if constexpr (has_p) prev[ap] = fmaf(k2.y, ddy, prev[ap]);
-                                    if constexpr (has_m) next[am] = fmaf(k2.z, ddy, next[am]);
-                                    if constexpr (has_p) next[ap] = fmaf(k2.w, ddy, next[ap]);
-                                }
-                            }
-                        }
-                    };
-                    // chunks of kChunk slots from the one holding fq; slots below fq carry zero
-                    // coupling constants and read finite (zeroed or earlier) shared memory
-                    auto chunk = [&](auto ci) {
-                        constexpr int C = decltype(ci)::value;
-                        static_for<kChunk>([&](auto ki) {
-                            slot(std::integral_constant<int, C * kChunk + decltype(ki)::value>{});
-                        });
-                    };
-                    switch (fq / kChunk) { RTPN_CHUNK_CASES(chunk) }
-                };
-                // at |m| = 0 only the cos type exists
-                if (Ms == 0)
-                    sweep(std::integral_constant<bool, TT == 0>{}, std::integral_constant<bool, O == 0>{});
-                else
-                    sweep(std::true_type{}, std::true_type{});
-            });
+            const float4* kown = reinterpret_cast<const float4*>(cf + cown);
+            const float4* koth = reinterpret_cast<const float4*>(cf + coth);
+            // sources q = fq .. NLB - 1 (q < fq has l < i: not in the column)
+            auto slot = [&](auto qi) {
+                constexpr int q = decltype(qi)::value;
+                if constexpr (q < NLB) {
+                    constexpr int ls = 2 * q + B;
+                    constexpr int lm = (ls - 1) / 2, lp = (ls + 1) / 2;  // acc index of l-1, l+1
+                    constexpr bool has_m = ls - 1 >= 0 && lm < NLA;
+                    constexpr bool has_p = ls + 1 <= N && lp < NLA;
+                    if constexpr (has_m || has_p) {
+                        if (!RTPN_SCHECK(q - fq >= -(kChunk - 1) && q - fq < column_len(N, i, B))) return;
+                        constexpr int am = has_m ? lm : 0, ap = has_p ? lp : 0;
+                        const float c = lds<S>(pc, q * UB);
+                        const float ddx = lds<S>(px, q * UB) - c;
+                        const float ddz = lds<S>(pz, q * UB) - c;
+                        const float4 k0 = kown[3 * q], k1 = kown[3 * q + 1];
+                        const float co = lds<S>(po, q * UB);
+                        const float ddy = lds<S>(py, q * UB) - co;
+                        const float4 k2 = koth[3 * q + 2];
+                        if constexpr (has_m) cur[am] = fmaf(k0.x, ddz, cur[am]);
+                        if constexpr (has_p) cur[ap] = fmaf(k0.y, ddz, cur[ap]);
+                        if constexpr (has_m) prev[am] = fmaf(k0.z, ddx, prev[am]);
+                        if constexpr (has_p) prev[ap] = fmaf(k0.w, ddx, prev[ap]);
+                        if constexpr (has_m) next[am] = fmaf(k1.x, ddx, next[am]);
+                        if constexpr (has_p) next[ap] = fmaf(k1.y, ddx, next[ap]);
+                        if constexpr (has_m) prev[am] = fmaf(k2.x, ddy, prev[am]);
+                        if constexpr (has_p) prev[ap] = fmaf(k2.y, ddy, prev[ap]);
+                        if constexpr (has_m) next[am] = fmaf(k2.z, ddy, next[am]);
+                        if constexpr (has_p) next[ap] = fmaf(k2.w, ddy, next[ap]);
+                    }
+                }
+            };
+            // chunks of kChunk slots from the one holding fq; slots below fq carry zero coupling
+            // constants and read finite (zeroed or earlier) shared memory
+            auto chunk = [&](auto ci) {
+                constexpr int C = decltype(ci)::value;
+                static_for<kChunk>([&](auto ki) { slot(std::integral_constant<int, C * kChunk + decltype(ki)::value>{}); });
+            };
+            switch (fq / kChunk) { RTPN_CHUNK_CASES(chunk) }
         }
-        if (fin) {
+        if (finw) {
             // ---- finish target column M = i - 1 (its accumulators are in prev), Eq. (5); the old
-            // values are the column's tile boxes in this stage
+            // values are the column's tile plane boxes in this stage
             const int M = i - 1;
             const float alpha = (M & 1) ? alO : alE, beta = (M & 1) ? beO : beE;
-            S* tp = tgt_ptr(M);
+            // u_0 (class 0, l = 0: slot 0 of column 0, cos type) takes its own factors and source
+            const bool u0 = A == 0 && M == 0 && T == 0;
+            S* tp = reinterpret_cast<S*>(a.tgt) +
+                    (long long)(cA0 + offA + T * column_len(N, M, A) - first_l(M, A) / 2) * V + cell;
             (void)RTPN_SCHECK(offA == colA[M]);
             const int q0 = first_l(M, A) / 2;  // targets q = q0 .. NLA - 1 (l >= M)
-            const unsigned char* ob = buf + L::TGTO + T * L::R_TGT + my - q0 * L::CTR_BYTES;
+            const unsigned char* ob = buf + tgo - q0 * UB;
             auto tslot = [&](auto qi) {
                 constexpr int q = decltype(qi)::value;
                 if constexpr (q < NLA) {
-                    const float old = lds<S>(ob, q * L::CTR_BYTES);
+                    const float old = lds<S>(ob, q * UB);
                     if constexpr (MODE == ADJ_TARGETS) {
                         const float la = lpre[q];
                         const float r = -a.inv_h * prev[q];  // the forward residual (without q)
                         const long long loc = (long long)(offA + T * column_len(N, M, A) - q0 + q) * V + cell;
                         float al, be;
-                        if (A == 0 && q == 0 && M == 0) {
+                        if (q == 0 && u0) {
                             g0 = fmaf(la, fmaf(da0, old, db0 * (r + q0s)), g0);
                             gqa = fmaf(be0, la, gqa);
                             al = al0;
@@ -698,17 +693,19 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                             al = alpha;
                             be = beta;
                         }
-                        a.wout[loc] = be * la;
-                        a.lam[(long long)cA0 * V + loc] = al * la;
+                        if (active) {
+                            a.wout[loc] = be * la;
+                            a.lam[(long long)cA0 * V + loc] = al * la;
+                        }
                     } else {
                         float nv;
                         if constexpr (MODE == ADJ_SOURCES)
                             nv = fmaf(a.inv_h, prev[q], old);
-                        else if (A == 0 && q == 0 && M == 0)
-                            nv = fmaf(al0, old, fmaf(-be0, prev[q], ga0));
+                        else if (q == 0)
+                            nv = u0 ? fmaf(al0, old, fmaf(-be0, prev[q], ga0)) : fmaf(alpha, old, -beta * prev[q]);
                         else
                             nv = fmaf(alpha, old, -beta * prev[q]);
-                        win::store<S>(tp + (long long)q * V, nv);
+                        if (active) win::store<S>(tp + (long long)q * V, nv);
                     }
                 }
             };
@@ -721,35 +718,39 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
             b = 0;
             ph ^= 1u;
         }
-        // shift the window: prev <- cur <- next <- 0
+        // prev is done: it is the next stage's `next`
 #pragma unroll
-        for (int q = 0; q < NLA; ++q) {
-            prev[q] = cur[q];
-            cur[q] = next[q];
-            next[q] = 0.f;
-        }
+        for (int q = 0; q < NLA; ++q) prev[q] = 0.f;
         if (i >= 1) offA += ntypes(i - 1) * column_len(N, i - 1, A);
         if constexpr (MODE == ADJ_TARGETS) {
-            if (i == NST - 1 && active) {
-                // this tile's media-gradient sums: each (cell, slot code) belongs to one thread
+            if (i == NST - 1) {
+                // this tile's media-gradient sums: each (cell, slot code) belongs to one thread; a
+                // thread past the grid's edge has summed values of no cell and only clears them
+                if (active) {
 #pragma unroll
-                for (int par = 0; par < 2; ++par) {
-                    const int gx = ((par == 0) == (T == 0)) ? 0 : 1;
-                    const int gz = ((A + par) & 1) == 0 ? 0 : 1;
-                    a.gacc[(long long)(gx + 2 * T + 4 * gz) * V + cell] += (double)(par == 0 ? gE : gO);
-                }
-                if (A == 0 && T == 0) {
-                    a.gacc[8ll * V + cell] += (double)g0;
-                    a.gq[cell] += (double)gqa;
+                    for (int par = 0; par < 2; ++par) {
+                        const int gx = ((par == 0) == (T == 0)) ? 0 : 1;
+                        const int gz = ((A + par) & 1) == 0 ? 0 : 1;
+                        a.gacc[(long long)(gx + 2 * T + 4 * gz) * V + cell] += (double)(par == 0 ? gE : gO);
+                    }
+                    if (A == 0 && T == 0) {
+                        a.gacc[8ll * V + cell] += (double)g0;
+                        a.gq[cell] += (double)gqa;
+                    }
                 }
                 gE = gO = g0 = gqa = 0.f;
             }
         }
-        if (i == NST - 1) {  // tile done: reset the window and the column offset
-#pragma unroll
-            for (int q = 0; q < NLA; ++q) prev[q] = cur[q] = 0.f;
-            offA = 0;
-        }
+        if (i == NST - 1) offA = 0;  // tile done
+        ++s;
+        i = (i == NST - 1) ? 0 : i + 1;
+        return true;
+    };
+    // the column loop unrolled by three: the window's roles rotate instead of its registers moving
+    while (s < total) {
+        if (!stage(wa, wb, wc) || s >= total) break;
+        if (!stage(wb, wc, wa) || s >= total) break;
+        if (!stage(wc, wa, wb)) break;
     }
 }
 

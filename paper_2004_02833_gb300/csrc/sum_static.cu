@@ -55,20 +55,44 @@ __global__ void k_chunks_total(const double* __restrict__ partial, int count, do
     }
 }
 
-// Device address of g_sum_scratch for the current device, looked up once per device.
+// The driver's current context, through the runtime's entry-point query (no link to libcuda).
+typedef int (*CtxGetCurrentFn)(void** ctx);
+CtxGetCurrentFn ctx_get_current() {
+    static std::once_flag once;
+    static CtxGetCurrentFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    });
+    return fn;
+}
+
+// Device address of g_sum_scratch on the current device, looked up once per device and context
+// (the set-up): a device reset or a new primary context gets a fresh lookup, never a stale address.
 int scratch_address(double** out) {
     static std::mutex mu;
     static double* addr[256] = {};
+    static void* owner[256] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return (int)e;
     if (dev < 0 || dev >= 256) return (int)cudaErrorInvalidDevice;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (!get) return (int)cudaErrorDeviceUninitialized;
+    void* cur = nullptr;
+    if (get(&cur) != 0) return (int)cudaErrorDeviceUninitialized;
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!cur || !addr[dev] || owner[dev] != cur) {
+        // the lookup also makes the device's primary context current on this thread
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_sum_scratch);
         if (e != cudaSuccess) return (int)e;
+        if (get(&cur) != 0 || !cur) return (int)cudaErrorDeviceUninitialized;
         addr[dev] = (double*)p;
+        owner[dev] = cur;
     }
     *out = addr[dev];
     return 0;

@@ -69,6 +69,7 @@ SIGNATURES = {
     "rtpn_synchronize": (_I, [_P]),
     "rtpn_test_wait_timeout": (_I, [_P, _I, ctypes.c_longlong]),
     "rtpn_adjoint": (_I, [_P, _P, _I, _I, _I, _I, _P, _P, _P, _I, ctypes.POINTER(_D)]),
+    "rtpn_detector": (_I, [_P, _P, _I, _I, _P, _I]),
     "rtpn_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _P, _P, _I]),
     "rtpn_batch_destroy": (_I, [_P]),
     "rtpn_batch_count": (_I, [_P]),
@@ -152,8 +153,13 @@ def sum_static(x, out, stream=None):
     out, without any allocation by the library (see rtpn_sum_static in include/rtpn.h)."""
     import torch
 
-    if not (x.is_cuda and out.is_cuda and out.dtype == torch.float64 and x.is_contiguous()):
-        raise ValueError("x must be a contiguous CUDA tensor and out a CUDA float64 tensor")
+    # checked before anything reaches the library: the kernel reads x.numel() values of 4 or 8 bytes
+    if x.dtype not in (torch.float32, torch.float64):
+        raise TypeError(f"sum_static sums float32 or float64 tensors, not {x.dtype}")
+    if out.dtype != torch.float64 or out.numel() < 1:
+        raise ValueError("out must hold at least one float64 value")
+    if not (x.is_cuda and out.is_cuda and x.is_contiguous()):
+        raise ValueError("x must be a contiguous CUDA tensor and out a CUDA tensor")
     code = DTYPE_F64 if x.dtype == torch.float64 else DTYPE_F32
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -298,6 +304,22 @@ class Context:
         self._chk(lib().rtpn_adjoint(self._p, ptr, code, where, int(k), int(ckpt_every), bufs[0][0],
                                      bufs[1][0], bufs[2][0], ow.pop(), ctypes.byref(J)))
         return J.value, out
+
+    def detector(self, w, out=None):
+        """J = sum w u_0 on the current state (FP64, fixed order).  With `out` (a one-element float64
+        CUDA tensor) J is written there without a host synchronisation and `out` is returned;
+        otherwise J is returned as a Python float."""
+        ptr, code, where, keep = _buf(w)
+        if out is None:
+            J = _D()
+            self._chk(lib().rtpn_detector(self._p, ptr, code, where, ctypes.cast(ctypes.byref(J), _P), HOST))
+            return J.value
+        import torch
+
+        if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1):
+            raise ValueError("out must be a CUDA float64 tensor with at least one element")
+        self._chk(lib().rtpn_detector(self._p, ptr, code, where, _P(out.data_ptr()), DEVICE))
+        return out
 
     def sum_u0(self) -> float:
         out = _D()

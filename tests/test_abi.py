@@ -81,3 +81,30 @@ def test_new_entry_points_reject_a_null_context(rtpn_lib):
     # no GPU needed: argument checks come before any device call
     assert rtpn_lib.rtpn_set_spacing(None, 0.1, 0.1, 0.1) == rtpn.EINVAL
     assert rtpn_lib.rtpn_set_scattering(None, None, 0) == rtpn.EINVAL
+
+
+def test_sum_static_refuses_other_dtypes_before_any_launch(rtpn_lib):
+    # the kernel reads numel() values of 4 or 8 bytes: a bf16 / f16 / integer tensor, or an empty
+    # output, is refused by the binding before the library is called (CPU tensors suffice here)
+    import torch
+
+    out = torch.zeros(1, dtype=torch.float64)
+    for dt in (torch.bfloat16, torch.float16, torch.int32, torch.int64):
+        with pytest.raises(TypeError):
+            rtpn.sum_static(torch.zeros(8, dtype=dt), out)
+    with pytest.raises(ValueError):
+        rtpn.sum_static(torch.zeros(8, dtype=torch.float32), torch.zeros(0, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        rtpn.sum_static(torch.zeros(8, dtype=torch.float32), torch.zeros(1, dtype=torch.float32))
+
+
+def test_autograd_form_refuses_host_tensors():
+    # the autograd wrapper hands device pointers to the library: host tensors are refused before
+    # any call reaches it
+    import torch
+
+    from paper_2004_02833_gb300.autograd import detector_response
+
+    t = torch.zeros((2, 2, 2), dtype=torch.float64, requires_grad=True)
+    with pytest.raises(TypeError):
+        detector_response(None, t, t, t, torch.zeros((4, 2, 2, 2), dtype=torch.float64), t.detach(), 1)

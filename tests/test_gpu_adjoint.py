@@ -1,11 +1,10 @@
 """Adjoint form: GPU discrete adjoint vs the oracle's discrete adjoint and vs central finite
 differences of the GPU forward.
 
-Bounds: FP64 storage: J and the final state <= 1e-12 relative to the oracle; each gradient <= 1e-11
-relative in max norm (an entry sums ~10^3 FP64 products over substeps, components and the point
-means, in a different order than the oracle: ~10^3 * 1.1e-16 times the cancellation of the sum);
-FP32 storage <= 1e-4 relative to the oracle's exact adjoint; FP32 adjoint vs FP64 central
-differences <= 1e-3.
+Bounds: FP64 storage: J, the final state and each gradient <= 1e-12 relative (max norm) to the
+oracle, the bound the task sets for FP64 parity (both sides evaluate E' of Eq. 5, which enters
+dbeta/dc, without the cancellation of its closed form near 0); FP32 storage <= 1e-4 relative to the
+oracle's exact adjoint; FP32 adjoint vs FP64 central differences <= 1e-3.
 """
 import numpy as np
 import pytest
@@ -21,7 +20,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("bc", ["periodic", "vacuum"])
-@pytest.mark.parametrize("precision,tol,gtol", [("fp64", 1e-12, 1e-11), ("fp32", 1e-4, 1e-4)])
+@pytest.mark.parametrize("precision,tol,gtol", [("fp64", 1e-12, 1e-12), ("fp32", 1e-4, 1e-4)])
 def test_adjoint_matches_oracle(cuda_device, coupling_cache, bc, precision, tol, gtol):
     N, shape = 3, (5, 6, 8)
     inst, u0 = synth.random_instance(N, shape, seed=41, bc=bc)
@@ -59,6 +58,26 @@ def test_adjoint_staged_kernel_fp32_vs_oracle(cuda_device, coupling_cache, bc):
     assert rel(gsa, gsa_ref) <= 1e-4 and rel(gss, gss_ref) <= 1e-4 and rel(gq, gq_ref) <= 1e-4
 
 
+@pytest.mark.parametrize("bc", ["periodic", "vacuum"])
+def test_adjoint_staged_kernel_many_tiles_vs_oracle(cuda_device, coupling_cache, bc):
+    # more tiles than CTAs (one per SM), partial tiles in x and z: the per-tile media-gradient sums
+    # of the staged pull-back must start from zero on every tile a CTA walks
+    N, shape = 7, (9, 40, 72)
+    inst, u0 = synth.random_instance(N, shape, seed=45, bc=bc)
+    w = np.random.default_rng(46).uniform(0.0, 1.0, shape)
+    mats, slots = coupling_cache(N)
+    P = st.Problem(N, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, bc, mats=mats, slots=slots)
+    J_ref, gsa_ref, gss_ref, gq_ref = P.gradient(u0, 2, w)
+    with rtpn.Context(N, shape, inst.h, bc, "fp32", inst.dt) as ctx:
+        ctx.set_kernel("stage", (32, 2, 2))
+        assert ctx.info().kernel == 3
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        J, (gsa, gss, gq) = ctx.adjoint(w, 2, ckpt_every=1)
+    assert abs(J - J_ref) <= 1e-4 * abs(J_ref)
+    assert rel(gsa, gsa_ref) <= 1e-4 and rel(gss, gss_ref) <= 1e-4 and rel(gq, gq_ref) <= 1e-4
+
+
 def test_adjoint_p3_32_checkerboard_fp64(cuda_device, coupling_cache):
     # P3 on 32^3 in FP64: the lattice scaled to 32^3, vacuum, zero start, detector box scaled
     inst = synth.checkerboard(3, 32)
@@ -71,7 +90,7 @@ def test_adjoint_p3_32_checkerboard_fp64(cuda_device, coupling_cache):
         ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
         J, (gsa, gss, gq) = ctx.adjoint(w, k, ckpt_every=7)
     assert J_ref > 0 and abs(J - J_ref) <= 1e-12 * J_ref
-    assert rel(gsa, gsa_ref) <= 1e-11 and rel(gss, gss_ref) <= 1e-11 and rel(gq, gq_ref) <= 1e-11
+    assert rel(gsa, gsa_ref) <= 1e-12 and rel(gss, gss_ref) <= 1e-12 and rel(gq, gq_ref) <= 1e-12
 
 
 def test_adjoint_fp32_vs_central_differences(cuda_device):
@@ -107,3 +126,49 @@ def test_adjoint_fp32_vs_central_differences(cuda_device):
             fd = (J64(p["sa"], p["ss"], p["q"]) - J64(m["sa"], m["ss"], m["q"])) / (2 * eps)
             scale = max(abs(fd), 1e-3 * np.abs(g).max())
             assert abs(g[cell] - fd) <= 1e-3 * scale, (name, cell, g[cell], fd)
+
+
+def test_adjoint_p15_96_config_vs_central_differences(cuda_device):
+    # The adjoint workload at its stated size: P15 on the [0,7]^3 lattice at 96^3 cells, vacuum, 200
+    # steps with checkpoints every 20, J = sum of u_0 over the 12^3 detector box.
+    #  * the method: the FP64 adjoint (the oracle's discrete adjoint to 1e-12, tests above) against
+    #    central differences of the FP64 forward (perturbation 1e-6 max(sigma, 1)) at 20 cells drawn
+    #    by default_rng(4) from the region between the source block (3,3,3) and the detector block
+    #    (5,3,3), all three media fields at each: <= 1e-5 of max(|fd|, 1e-3 max|g|);
+    #  * the precision: the FP32 adjoint against the FP64 one over the whole grid, normwise, J to
+    #    1e-4 and each gradient field to 1e-3 of its max.
+    N, n, k = 15, 96, 200
+    inst = synth.checkerboard(N, n)
+    w = synth.detector_box(n)
+    grads = {}
+    for prec in ("fp32", "fp64"):
+        with rtpn.Context(N, inst.shape, inst.h, inst.bc, prec, inst.dt) as ctx:
+            ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+            grads[prec] = ctx.adjoint(w, k, ckpt_every=20)
+    J32, g32 = grads["fp32"]
+    J64, g64 = grads["fp64"]
+    assert J64 > 0 and abs(J32 - J64) <= 1e-4 * J64
+    for a32, a64 in zip(g32, g64):
+        assert rel(a32, a64) <= 1e-3
+    rng = np.random.default_rng(4)
+    cells = list(zip(rng.integers(41, 55, 20), rng.integers(41, 55, 20), rng.integers(41, 82, 20)))
+    with rtpn.Context(N, inst.shape, inst.h, inst.bc, "fp64", inst.dt) as c64:
+
+        def J(sa, ss, q):
+            c64.set_media(sa, ss, q)
+            c64.zero_moments()
+            c64.step(k)
+            return c64.detector(w)
+
+        assert abs(J(inst.sigma_a, inst.sigma_s, inst.q) - J64) <= 1e-12 * J64
+        for cell in [(int(z), int(y), int(x)) for z, y, x in cells]:
+            for name, g in zip(("sa", "ss", "q"), g64):
+                args = {"sa": inst.sigma_a, "ss": inst.sigma_s, "q": inst.q}
+                eps = 1e-6 * max(float(args[name][cell]), 1.0)
+                p = {kk: v.copy() for kk, v in args.items()}
+                m = {kk: v.copy() for kk, v in args.items()}
+                p[name][cell] += eps
+                m[name][cell] -= eps
+                fd = (J(p["sa"], p["ss"], p["q"]) - J(m["sa"], m["ss"], m["q"])) / (2 * eps)
+                scale = max(abs(fd), 1e-3 * np.abs(g).max())
+                assert abs(g[cell] - fd) <= 1e-5 * scale, (name, cell, g[cell], fd)

@@ -218,15 +218,20 @@ STAGE_CASES = [
     # N, shape (nz, ny, nx) with nx a multiple of 8, bc, tile (0 = default), stage buffers (0 = any)
     (7, (9, 13, 72), "vacuum", (0, 0, 0), 0),
     (7, (5, 6, 32), "periodic", (0, 0, 0), 0),
-    (15, (7, 9, 40), "periodic", (32, 4, 2), 4),
-    (15, (3, 5, 8), "vacuum", (32, 4, 2), 0),
+    (15, (7, 9, 40), "periodic", (32, 2, 2), 4),
+    (15, (3, 5, 8), "vacuum", (32, 2, 2), 0),
+    (15, (5, 3, 136), "periodic", (64, 2, 2), 3),
+    (15, (4, 7, 16), "vacuum", (64, 2, 2), 3),
     (39, (5, 6, 8), "periodic", (32, 2, 2), 3),
     (39, (5, 7, 8), "vacuum", (40, 2, 2), 2),
     (39, (3, 5, 80), "periodic", (40, 2, 2), 2),
     (39, (4, 3, 72), "vacuum", (40, 2, 2), 0),
     (39, (7, 5, 120), "periodic", (40, 2, 2), 2),
-    (39, (3, 5, 120), "periodic", (80, 2, 1), 2),
-    (39, (4, 3, 160), "vacuum", (80, 2, 1), 2),
+    (39, (3, 5, 120), "periodic", (32, 2, 2), 3),
+    (39, (4, 3, 160), "vacuum", (32, 2, 2), 3),
+    # more tiles than CTAs (one per SM): CTAs walk several tiles, partial ones among them
+    (7, (12, 44, 72), "vacuum", (32, 2, 2), 4),
+    (15, (9, 30, 72), "periodic", (32, 2, 2), 4),
 ]
 
 
