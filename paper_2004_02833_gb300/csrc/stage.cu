@@ -21,9 +21,12 @@ namespace {
 
 constexpr int kN = RTPN_SN, kTX = RTPN_STX, kTY = RTPN_STY, kTZ = RTPN_STZ, kNB = RTPN_SNB, kEM = RTPN_SEM;
 constexpr int kThreads = Layout<kN, 0, float, kTX, kTY, kTZ, kNB, kEM>::THREADS;
+// Two CTAs per SM where two rings fit shared memory and the order's window fits the registers
+// that leaves (orders up to 15: about 110 registers a thread); one otherwise.
+constexpr int kMinBlocks = (kN <= 15 && 2 * Layout<kN, 0, float, kTX, kTY, kTZ, kNB, kEM>::BYTES <= 232448) ? 2 : 1;
 
 template <int A, typename S, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) k_stage(Args a) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_stage(Args a) {
     static_assert(Layout<kN, A, S, kTX, kTY, kTZ, kNB, kEM>::FITS, "stage ring exceeds shared memory");
     extern __shared__ __align__(128) unsigned char smem[];
     stage_kernel_body<kN, A, S, kTX, kTY, kTZ, kNB, kEM, MODE>(a, smem);

@@ -41,7 +41,7 @@ def test_autograd_p3_32_checkerboard_fp64_vs_oracle(cuda_device, coupling_cache)
         J = detector_response(ctx, sa, ss, q, u0, wt, k, ckpt_every=7)
         gsa, gss, gq = torch.autograd.grad(J, (sa, ss, q))
         assert J.dim() == 0 and J.is_cuda
-        Jv = float(J)
+        Jv = float(J.detach())
     assert J_ref > 0 and abs(Jv - J_ref) <= 1e-12 * J_ref
     for g, ref in ((gsa, gsa_ref), (gss, gss_ref), (gq, gq_ref)):
         assert rel(g.cpu().numpy(), ref) <= 1e-12
@@ -62,7 +62,7 @@ def test_autograd_scales_by_the_incoming_gradient(cuda_device):
         ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
         ctx.set_moments(u)
         J_plain, (gsa, gss, gq) = ctx.adjoint(w, 4, ckpt_every=3)
-    assert abs(float(J) - J_plain) <= 1e-13 * abs(J_plain)
+    assert abs(float(J.detach()) - J_plain) <= 1e-13 * abs(J_plain)
     for t, g in ((sa, gsa), (ss, gss), (q, gq)):
         assert np.array_equal(t.grad.cpu().numpy(), 2.5 * g)
 
@@ -99,6 +99,6 @@ def test_autograd_fp32_staged_vs_oracle(cuda_device, coupling_cache):
         J = detector_response(ctx, sa, ss, q, u0, wt, 3, ckpt_every=2)
         gsa, gss, gq = torch.autograd.grad(J, (sa, ss, q))
     assert gsa.dtype == torch.float32
-    assert abs(float(J) - J_ref) <= 1e-4 * abs(J_ref)
+    assert abs(float(J.detach()) - J_ref) <= 1e-4 * abs(J_ref)
     for g, ref in ((gsa, gsa_ref), (gss, gss_ref), (gq, gq_ref)):
         assert rel(g.cpu().double().numpy(), ref) <= 1e-4

@@ -11,7 +11,7 @@ import pytest
 from oracle import stepper as st
 from paper_2004_02833_gb300 import rtpn, synth
 
-from test_gpu_parity import bf16_tol
+from test_gpu_parity import assert_parity, bf16_random_walk
 
 pytestmark = pytest.mark.gpu
 
@@ -72,19 +72,21 @@ def test_config2_small_instance_vs_oracle(cuda_device):
     # P39 on an independent 24^3 instance with the 200^3 rules, 100 steps: GPU FP64 vs the oracle
     inst = synth.random_blocks(39, 24, seed=2)
     u0 = inst.full_state()
-    ref = st.Problem(39, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, inst.bc).run(u0, 100)
-    for precision, tol in (("fp64", 1e-12), ("fp32", 1e-5), ("bf16", bf16_tol(100))):
+    P = st.Problem(39, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, inst.bc)
+    ref = P.run(u0, 100)
+    for precision in ("fp64", "fp32", "bf16"):
         with make(inst, precision) as ctx:
             ctx.set_moments(u0)
             ctx.step(100)
             got = ctx.get_moments()
-        err = np.abs(got - ref).max() / np.abs(ref).max()
-        assert err <= tol, (precision, err)
+        assert_parity(got, ref, precision, P, u0, 100)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", bf16_tol(100))])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", bf16_random_walk(100))])
 def test_config2_full_size_vs_gpu_fp64(cuda_device, precision, tol):
-    # P39 200^3 periodic, 100 steps: FP32 / BF16 storage vs the GPU FP64 path on the same input
+    # P39 200^3 periodic, 100 steps: FP32 / BF16 storage vs the GPU FP64 path on the same input.
+    # No oracle runs at this size, so BF16 is held to the random-walk size of its storage rounding
+    # (an estimate, see bf16_random_walk); its rounding model is checked on the 24^3 instance.
     import torch
 
     inst = synth.random_blocks(39, 200, seed=2)

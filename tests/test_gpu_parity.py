@@ -3,10 +3,14 @@
 Tolerances:
   * FP64 storage: max |u - u_ref| <= 1e-12 * max |u_ref| (the method's own bound for FP64 mode);
   * FP32 storage: <= 1e-5 * max |u_ref| after the runs below (the FP32 bound of the target);
-  * BF16 storage (FP32 math, RNE stores): every pass rounds the class it writes once, with unit
-    roundoff 2^-9; the step operator is non-expansive (|eig| <= 1 for dt < h/3, Section 2.1), so
-    independent roundings accumulate like a random walk over the 2k+1 passes of k steps.  The bound
-    is max(2e-2, 2 sqrt(2k+1) 2^-9) relative to max |u_ref| (``bf16_tol``).
+  * BF16 storage (FP32 arithmetic, round-to-nearest-even stores): checked against the rounding
+    model of the scheme, the oracle run with the same storage roundings (``bf16_model``: the
+    merged schedule of the library, each pass's class rounded to BF16 after it is written).  The
+    GPU applies the same roundings and differs from the model only where its FP32 arithmetic tips
+    a rounding the other way (about 2^-16 of the roundings, one BF16 ulp each, propagated by a
+    non-expansive step), so its L2 distance to the model must stay below a tenth of the model's
+    own L2 distance to the exact (FP64) result: the BF16 path adds nothing beyond storage
+    rounding.  The size of that rounding error itself is a measured result, not a pass/fail bound.
 """
 import numpy as np
 import pytest
@@ -16,12 +20,55 @@ from paper_2004_02833_gb300 import rtpn, synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 2e-2}
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
-def bf16_tol(steps: int) -> float:
-    """Storage-rounding bound for k steps of BF16 storage (see the module docstring)."""
-    return max(2e-2, 2.0 * (2 * steps + 1) ** 0.5 * 2.0 ** -9)
+def bf16_round(u):
+    """Round to the nearest BF16 value, ties to even (8 significant bits), through FP32."""
+    b = np.asarray(u, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_model(P, u0, k):
+    """The state after k steps of the library's schedule (odd dt/2, then (even dt, odd dt) k - 1
+    times, even dt, odd dt/2: Eq. 6 with neighbouring odd half steps merged) with BF16 storage: the
+    input rounded, and after every pass the class it wrote."""
+    u = bf16_round(u0)
+    if k == 0:
+        return u
+
+    def run(u, cls, tau):
+        u = P.substep(u, cls, tau)
+        m = P.cls == cls
+        u[m] = bf16_round(u[m])
+        return u
+
+    u = run(u, 1, 0.5 * P.dt)
+    for s in range(k):
+        u = run(u, 0, P.dt)
+        u = run(u, 1, P.dt if s < k - 1 else 0.5 * P.dt)
+    return u
+
+
+def bf16_random_walk(steps: int) -> float:
+    """The size of BF16 storage rounding after k steps of 2k + 1 passes, relative to max |u|:
+    each pass rounds the class it writes with unit roundoff u = 2^-8 (8 significant bits, round to
+    nearest), the step is non-expansive (|eig| <= 1 for dt < h/3, Section 2.1), and independent
+    roundings add like a random walk: sqrt(2k + 1) u.  An estimate of the typical size, used only
+    where the oracle cannot run (the 200^3 workload)."""
+    return (2 * steps + 1) ** 0.5 * 2.0 ** -8
+
+
+def assert_parity(got, ref, precision, P=None, u0=None, k=None):
+    """FP64 / FP32: normwise against the oracle.  BF16: against the rounding model (see above)."""
+    if precision != "bf16":
+        assert rel_err(got, ref) <= TOL[precision], (precision, rel_err(got, ref))
+        return
+    model = bf16_model(P, u0, k)
+    dev = float(np.linalg.norm(got - model))
+    eff = float(np.linalg.norm(model - ref))
+    assert dev <= 0.1 * eff, ("bf16", dev / max(eff, 1e-300), rel_err(got, ref))
 
 
 def rel_err(got, ref):
@@ -73,9 +120,10 @@ CASES = [
 @pytest.mark.parametrize("N,shape,bc,steps", CASES)
 def test_random_media_and_state(cuda_device, coupling_cache, N, shape, bc, steps, precision):
     inst, u0 = synth.random_instance(N, shape, seed=100 + N, bc=bc)
-    ref = oracle_problem(inst, coupling_cache).run(u0, steps)
+    P = oracle_problem(inst, coupling_cache)
+    ref = P.run(u0, steps)
     got = gpu_run(inst, u0, steps, precision)
-    assert rel_err(got, ref) <= TOL[precision], rel_err(got, ref)
+    assert_parity(got, ref, precision, P, u0, steps)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -175,9 +223,10 @@ def test_window_kernel_tiles(cuda_device, coupling_cache, tile):
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_window_p39(cuda_device, coupling_cache, bc, precision):
     inst, u0 = synth.random_instance(39, (5, 6, 7), seed=39, bc=bc)
-    ref = oracle_problem(inst, coupling_cache).run(u0, 2)
+    P = oracle_problem(inst, coupling_cache)
+    ref = P.run(u0, 2)
     got = gpu_run(inst, u0, 2, precision, kernel="window")
-    assert rel_err(got, ref) <= TOL[precision]
+    assert_parity(got, ref, precision, P, u0, 2)
 
 
 @pytest.mark.parametrize("N", [1, 3, 5, 9, 15])
@@ -240,7 +289,8 @@ STAGE_CASES = [
 def test_stage_kernel(cuda_device, coupling_cache, N, shape, bc, tile, depth, precision):
     # TMA-staged kernel: full and partial tiles, wrapped and zero-filled halos, pipeline depths
     inst, u0 = synth.random_instance(N, shape, seed=300 + N, bc=bc)
-    ref = oracle_problem(inst, coupling_cache).run(u0, 3)
+    P = oracle_problem(inst, coupling_cache)
+    ref = P.run(u0, 3)
     with rtpn.Context(N, inst.shape, inst.h, inst.bc, precision, inst.dt) as ctx:
         ctx.set_kernel("stage", tile, depth)
         info = ctx.info()
@@ -249,7 +299,7 @@ def test_stage_kernel(cuda_device, coupling_cache, N, shape, bc, tile, depth, pr
         ctx.set_moments(u0)
         ctx.step(3)
         got = ctx.get_moments()
-    assert rel_err(got, ref) <= TOL[precision], rel_err(got, ref)
+    assert_parity(got, ref, precision, P, u0, 3)
 
 
 def test_stage_depth_that_fits_bf16_only(cuda_device, coupling_cache):
@@ -259,7 +309,8 @@ def test_stage_depth_that_fits_bf16_only(cuda_device, coupling_cache):
         with pytest.raises(rtpn.RtpnError) as e:
             ctx.set_kernel("stage", (40, 2, 2), 4)
         assert e.value.code == rtpn.EUNSUPPORTED
-    ref = oracle_problem(inst, coupling_cache).run(u0, 3)
+    P = oracle_problem(inst, coupling_cache)
+    ref = P.run(u0, 3)
     with rtpn.Context(39, inst.shape, inst.h, inst.bc, "bf16", inst.dt) as ctx:
         ctx.set_kernel("stage", (40, 2, 2), 4)
         assert ctx.info().depth == 4
@@ -267,7 +318,7 @@ def test_stage_depth_that_fits_bf16_only(cuda_device, coupling_cache):
         ctx.set_moments(u0)
         ctx.step(3)
         got = ctx.get_moments()
-    assert rel_err(got, ref) <= TOL["bf16"], rel_err(got, ref)
+    assert_parity(got, ref, "bf16", P, u0, 3)
 
 
 def test_stage_kernel_long_run_matches_window(cuda_device):
@@ -316,7 +367,8 @@ def test_fused_kernel(cuda_device, coupling_cache, N, shape, bc, zc, steps, prec
     # several z chunks, zero or wrapped halos, odd and even numbers of passes (the state ends in
     # either buffer)
     inst, u0 = synth.random_instance(N, shape, seed=400 + N, bc=bc)
-    ref = oracle_problem(inst, coupling_cache).run(u0, steps)
+    P = oracle_problem(inst, coupling_cache)
+    ref = P.run(u0, steps)
     with rtpn.Context(N, inst.shape, inst.h, inst.bc, precision, inst.dt) as ctx:
         ctx.set_kernel("fused", (0, 0, zc))
         assert ctx.info().kernel == 4
@@ -325,7 +377,7 @@ def test_fused_kernel(cuda_device, coupling_cache, N, shape, bc, zc, steps, prec
         ctx.step(steps)
         got = ctx.get_moments()
         s0 = ctx.sum_u0()
-    assert rel_err(got, ref) <= TOL[precision], rel_err(got, ref)
+    assert_parity(got, ref, precision, P, u0, steps)
     assert abs(s0 - got[0].sum()) <= 1e-9 * max(1.0, abs(got[0]).sum())
 
 

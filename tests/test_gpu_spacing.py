@@ -10,7 +10,7 @@ from paper_2004_02833_gb300 import rtpn, synth
 pytestmark = pytest.mark.gpu
 
 H3 = (0.1, 0.13, 0.17)   # dt = 0.03 < min(h) / 3
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 2e-2}
+from test_gpu_parity import TOL, assert_parity  # noqa: E402
 
 
 def rel(a, b):
@@ -38,7 +38,8 @@ CASES = [
 @pytest.mark.parametrize("N,shape,bc,kernel,precision,kid", CASES)
 def test_non_cubic_cells_vs_oracle(cuda_device, coupling_cache, N, shape, bc, kernel, precision, kid):
     inst, u0 = synth.random_instance(N, shape, seed=1000 + N, bc=bc)
-    ref = problem(inst, coupling_cache).run(u0, 3)
+    P = problem(inst, coupling_cache)
+    ref = P.run(u0, 3)
     with rtpn.Context(N, shape, H3[0], bc, precision, inst.dt) as ctx:
         if kernel != "auto":
             ctx.set_kernel(kernel)
@@ -49,7 +50,7 @@ def test_non_cubic_cells_vs_oracle(cuda_device, coupling_cache, N, shape, bc, ke
         ctx.set_moments(u0)
         ctx.step(3)
         got = ctx.get_moments()
-    assert rel(got, ref) <= TOL[precision], rel(got, ref)
+    assert_parity(got, ref, precision, P, u0, 3)
 
 
 def test_spacing_back_to_cubic_is_bitwise_unchanged(cuda_device):
