@@ -141,40 +141,10 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
         ctx->stage_adj_lam = ctx->stage_adj_w = nullptr;  // the adjoint's maps follow the tile
     }
     if (!ctx->stage_mem) {
-        // per target class A: the coupling constants of the source class by column, type and slot q
-        // ([N+1][2][N/2+1][CPAD], see stage_impl.cuh), then the column starts of both classes
-        const int nl = N / 2 + 1;
-        std::vector<int> col(2 * (N + 2));
-        for (int P = 0; P < 2; ++P) {
-            int acc = 0;
-            for (int M = 0; M <= N + 1; ++M) {
-                col[P * (N + 2) + M] = acc;
-                if (M <= N) acc += win::ntypes(M) * win::column_len(N, M, P);
-            }
-        }
+        std::vector<int> col;
         std::vector<float> tab[2];
-        for (int A = 0; A < 2; ++A) {
-            const int B = 1 - A;
-            std::vector<float> t10;  // [local source index of class B][10]
-            if (!win::coef_table(ctx->md, A, &t10)) return (int)cudaErrorInvalidValue;
-            tab[A].assign((size_t)(N + 1) * 2 * nl * stg::CPAD, 0.f);
-            for (int M = 0; M <= N; ++M)
-                for (int t = 0; t < win::ntypes(M); ++t)
-                    for (int j = 0; j < win::column_len(N, M, B); ++j) {
-                        const int src = col[B * (N + 2) + M] + t * win::column_len(N, M, B) + j;
-                        // slot = the source's q = (l - B) / 2 (l = first l of the column + 2 j); slots of
-                        // l < M stay zero, so a sweep may start at a slot boundary below the column
-                        const int q = win::first_l(M, B) / 2 + j;
-                        float* d = &tab[A][(((size_t)M * 2 + t) * nl + q) * stg::CPAD];
-                        const float* k = &t10[(size_t)src * 10];
-                        // the kernel applies 1/h of x; z and y constants carry h / h_z, h / h_y
-                        // (exactly 1 for cubic cells)
-                        const double sz = ctx->g.h / ctx->g.hz, sy = ctx->g.h / ctx->g.hy;
-                        for (int r = 0; r < 2; ++r) d[r] = (float)(k[r] * sz);  // z
-                        for (int r = 2; r < 6; ++r) d[r] = k[r];                // x to M-1, x to M+1
-                        for (int r = 0; r < 4; ++r) d[8 + r] = (float)(k[6 + r] * sy);  // y to M-1, M+1
-                    }
-        }
+        if (!stg::coupling_tables(ctx->md, ctx->g.h / ctx->g.hy, ctx->g.h / ctx->g.hz, tab, &col))
+            return (int)cudaErrorInvalidValue;
         const size_t b0 = tab[0].size() * 4, b1 = tab[1].size() * 4, b2 = col.size() * 4;
         cudaError_t err = cudaMalloc(&ctx->stage_mem, b0 + b1 + b2);
         if (err != cudaSuccess) return (int)err;

@@ -172,13 +172,50 @@ struct Layout {
     static constexpr int BARS = pad128(2 * NB * 8);
     static constexpr int BYTES = NB * BUF + BARS + 128;   // ring, mbarriers, base alignment slack
     static_assert(TY == TZ, "every box kind has the volume TY * TX per component only if TY == TZ");
-    static_assert(XW > 0, "no 16-byte x halo group divides the tile width");
     static_assert(TX % G == 0, "tile width must be a multiple of the 16-byte group");
     static_assert(CELLS % 32 == 0, "a type's threads must fill whole warps");
     static_assert(NB >= 2 && NB <= 8, "two to eight stage buffers");
     static_assert(REG >= (kChunk - 1) * UB, "a region must cover what a chunked sweep reads below the next");
-    static constexpr bool FITS = BYTES <= 232448;  // 227 KB of shared memory per CTA
+    // the ring fits 227 KB of shared memory per CTA, and an x halo group exists for this element
+    // size (a tile too narrow for RY >= TY rows of 16-byte groups is compiled for FP32 only)
+    static constexpr bool FITS = BYTES <= 232448 && XW > 0;
 };
+
+// The coupling constants of the staged kernel (host; the library and its host check program):
+// per target class A, the constants of the source class by column, type and slot q
+// ([N+1][2][N/2+1][CPAD], layout above; slots of l < M stay zero, so a sweep may start at a slot
+// boundary below the column), from the model's coupling (win::coef_table).  The kernel applies
+// 1/h of x; the y and z constants carry sy = h / h_y and sz = h / h_z (exactly 1 for cubic
+// cells).  col: the first local index of column M in class P at col[P (N + 2) + M].
+inline bool coupling_tables(const Model& md, double sy, double sz, std::vector<float> tab[2], std::vector<int>* col) {
+    const int N = md.N, nl = N / 2 + 1;
+    col->assign(2 * (N + 2), 0);
+    for (int P = 0; P < 2; ++P) {
+        int acc = 0;
+        for (int M = 0; M <= N + 1; ++M) {
+            (*col)[P * (N + 2) + M] = acc;
+            if (M <= N) acc += ntypes(M) * column_len(N, M, P);
+        }
+    }
+    for (int A = 0; A < 2; ++A) {
+        const int B = 1 - A;
+        std::vector<float> t10;  // [local source index of class B][10]
+        if (!win::coef_table(md, A, &t10)) return false;
+        tab[A].assign((size_t)(N + 1) * 2 * nl * CPAD, 0.f);
+        for (int M = 0; M <= N; ++M)
+            for (int t = 0; t < ntypes(M); ++t)
+                for (int j = 0; j < column_len(N, M, B); ++j) {
+                    const int src = (*col)[B * (N + 2) + M] + t * column_len(N, M, B) + j;
+                    const int q = first_l(M, B) / 2 + j;  // the source's slot (l - B) / 2
+                    float* d = &tab[A][(((size_t)M * 2 + t) * nl + q) * CPAD];
+                    const float* kk = &t10[(size_t)src * 10];
+                    for (int r = 0; r < 2; ++r) d[r] = (float)(kk[r] * sz);          // z
+                    for (int r = 2; r < 6; ++r) d[r] = kk[r];                        // x to M-1, M+1
+                    for (int r = 0; r < 4; ++r) d[8 + r] = (float)(kk[6 + r] * sy);  // y to M-1, M+1
+                }
+    }
+    return true;
+}
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -229,8 +266,11 @@ __device__ __forceinline__ bool wait_phase(unsigned bar, unsigned parity, unsign
     return false;
 }
 
+// a stored value at base + byte_off of a stage buffer, as FP32 (host and device: the host check
+// program runs the consumers' column work over a bounds-checked copy of the buffer)
 template <typename S>
-__device__ __forceinline__ float lds(const unsigned char* base, int byte_off) {
+RTPN_HD float lds(const unsigned char* base, int byte_off) {
+    RTPN_CHECK_PTR(base + byte_off);
     if constexpr (sizeof(S) == 4) {
         return *reinterpret_cast<const float*>(base + byte_off);
     } else {
@@ -323,6 +363,92 @@ __host__ __device__ __forceinline__ TileGeo tile_geo(const Args& a, unsigned t) 
 // Source x slot: 1 (read at i+1 by its partners) iff (M even) == (cos type); z slot: 1 iff l+M even.
 __host__ __device__ __forceinline__ int dir_x(int M, int t) { return ((M & 1) == 0) == (t == 0) ? 1 : -1; }
 
+// ---------------------------------------------------------------- the stage plan
+// One TMA box of a stage: which tensor map (array, kind, box length), its start coordinates and
+// where it lands in the stage buffer.  Host and device: the producer issues it, the host check
+// program copies it.
+struct BoxJob {
+    int valid;    // 0: this job issues nothing in this stage
+    int target;   // 1: a plane box of the target array (map a.tmap + emap), 0: of the source array
+    int kind;     // MAP_PLANE, MAP_YROW or MAP_XGRP (source array)
+    int emap;     // box length index: E = EQ * (emap + 1) components
+    int x, y, z, c;
+    int dst;      // byte offset of the box in the stage buffer
+};
+
+// The runs of stage i, the same for every box of the stage: source column i of class B (length,
+// types present) and target column i - 1 of class A.
+struct StageRuns {
+    int len, nt, lenA, ntA;
+};
+template <int N, int A>
+RTPN_HD StageRuns stage_runs(int i) {
+    constexpr int B = 1 - A;
+    StageRuns r;
+    r.len = column_len(N, i, B);          // none at i = N + 1
+    r.nt = r.len > 0 ? ntypes(i) : 0;
+    r.lenA = i >= 1 ? column_len(N, i - 1, A) : 0;
+    r.ntA = r.lenA > 0 ? ntypes(i - 1) : 0;
+    return r;
+}
+
+// Box j of stage i (runs r) of the tile with geometry g; offB_s and offA_s are the first local
+// indices of source column i in class B and of target column i - 1 in class A.  Jobs
+// 0 .. 2 NKIND - 1: source boxes (type j / NKIND, kind j % NKIND: TZ tile planes, the y halo row,
+// the z halo plane, the x halo group); then the target planes (type, plane).
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ>
+RTPN_HD BoxJob stage_box(const Args& a, const TileGeo& g, int i, const StageRuns& r, int offA_s, int offB_s, int j) {
+    using L = Layout<N, A, S, TX, TY, TZ, NB, EQ>;
+    constexpr int B = 1 - A;
+    constexpr int NK = L::NKIND;
+    BoxJob bj{0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (j >= 2 * NK) {  // target plane lz of type t
+        const int t = (j - 2 * NK) / TZ, lz = (j - 2 * NK) % TZ;
+        if (j >= 2 * NK + 2 * TZ || t >= r.ntA) return bj;
+        bj.valid = 1;
+        bj.target = 1;
+        bj.kind = MAP_PLANE;
+        bj.emap = (r.lenA + EQ - 1) / EQ - 1;
+        bj.x = g.x0;
+        bj.y = g.y0;
+        bj.z = g.z0 + lz;
+        bj.c = (A == 0 ? 0 : class_size(N, 0)) + offA_s + t * r.lenA;
+        bj.dst = L::TGTO + t * L::TGT_T + lz * L::REG;
+        return bj;
+    }
+    const int t = j / NK, k = j % NK;
+    if (t >= r.nt) return bj;
+    bj.valid = 1;
+    bj.emap = (r.len + EQ - 1) / EQ - 1;
+    bj.c = a.src_c0 + offB_s + t * r.len;  // first component of the run
+    bj.dst = L::SRCO + t * L::SRC_T + k * L::REG;
+    bj.x = g.x0;
+    bj.y = g.y0;
+    bj.z = g.z0;
+    if (k < TZ) {               // tile plane z0 + k
+        bj.kind = MAP_PLANE;
+        bj.z = g.z0 + k;
+    } else if (k == L::KY) {    // cos-type sources are read at y+1, sin-type at y-1
+        bj.kind = MAP_YROW;
+        bj.y = t == 0 ? g.hc[1][1] : g.hc[1][0];
+    } else if (k == L::KZ) {    // z slot 1 (l + M even) is read at z+1
+        bj.kind = MAP_PLANE;
+        bj.z = ((B + i) & 1) == 0 ? g.hc[2][1] : g.hc[2][0];
+    } else {                    // x slot 1 is read at x+1 (upper halo group)
+        bj.kind = MAP_XGRP;
+        bj.x = dir_x(i, t) > 0 ? g.hx_start[1] : g.hx_start[0];
+    }
+    return bj;
+}
+
+// bytes the boxes and the coupling constants of a stage with runs r bring into the buffer
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ>
+RTPN_HD unsigned stage_bytes(const StageRuns& r) {
+    using L = Layout<N, A, S, TX, TY, TZ, NB, EQ>;
+    const int ebox = (r.len + EQ - 1) / EQ * EQ, eboxA = (r.lenA + EQ - 1) / EQ * EQ;
+    return (unsigned)((r.nt * L::NKIND * ebox + r.ntA * TZ * eboxA) * L::UB) + (r.nt > 0 ? (unsigned)L::COEF_COL : 0u);
+}
+
 // The producer warp: issues the copies of every stage of this CTA's sequence into the ring.
 template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ>
 __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* bufs, unsigned full0,
@@ -330,12 +456,9 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
     using L = Layout<N, A, S, TX, TY, TZ, NB, EQ>;
     constexpr int B = 1 - A;
     constexpr int NST = N + 2;
-    constexpr int NK = L::NKIND;
-    constexpr int NJOB = 2 * NK + 2 * TZ;  // source boxes (type, kind), then target planes (type, z)
+    constexpr int NJOB = 2 * L::NKIND + 2 * TZ;  // source boxes (type, kind), then target planes (type, z)
     static_assert(NJOB <= 32, "one box per lane");
     const int lane = threadIdx.x & 31;
-    const int cA0 = A == 0 ? 0 : class_size(N, 0);
-    const int cB0 = a.src_c0;
     const CUtensorMap* maps = a.maps;
     // first local index of source column i in class B and of target column i - 1 in class A,
     // advanced column by column (no table loads on the producer's path)
@@ -377,59 +500,160 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
         if (i >= 1) offA += ntypes(i - 1) * column_len(N, i - 1, A);
         if (s == a.skip_stage) continue;
         unsigned char* buf = bufs + bcur * L::BUF;
-        const int len = column_len(N, i, B);     // sources of column i (none at i = N + 1)
-        const int nt = len > 0 ? ntypes(i) : 0;  // source types present in the column
-        const int ebox = (len + EQ - 1) / EQ * EQ;
-        const int M = i - 1;                     // target column finished in this stage
-        const int lenA = M >= 0 ? column_len(N, M, A) : 0;
-        const int ntA = lenA > 0 ? ntypes(M) : 0;
-        const int eboxA = (lenA + EQ - 1) / EQ * EQ;
-        const unsigned bytes = (unsigned)((nt * NK * ebox + ntA * TZ * eboxA) * L::UB) +
-                               (nt > 0 ? (unsigned)L::COEF_COL : 0u);
-        if (lane == 0) mbar_expect_tx(full, bytes);
-        __syncwarp();
-        if (lane < NJOB) {
-            const int j = lane;
-            if (j >= 2 * NK) {  // target plane lz of type t
-                const int t = (j - 2 * NK) / TZ, lz = (j - 2 * NK) % TZ;
-                if (t < ntA) {
-                    const int c = cA0 + offA_s + t * lenA;
-                    if (RTPN_SCHECK_ID(c >= 0 && c < a.nc && eboxA <= L::NL, 111, c))
-                        tma_load_4d(smem_addr(buf + L::TGTO + t * L::TGT_T + lz * L::REG), a.tmap + (eboxA / EQ - 1),
-                                    g.x0, g.y0, g.z0 + lz, c, full);
+        // one lane issues the stage: the box list is unrolled at compile time, so the kind of every
+        // box and its tensor map are fixed per box and all operands are the same for the warp
+        if (lane == 0) {
+            const StageRuns runs = stage_runs<N, A>(i);
+            mbar_expect_tx(full, stage_bytes<N, A, S, TX, TY, TZ, NB, EQ>(runs));
+            static_for<NJOB>([&](auto jj) {
+                constexpr int j = decltype(jj)::value;
+                const BoxJob bj = stage_box<N, A, S, TX, TY, TZ, NB, EQ>(a, g, i, runs, offA_s, offB_s, j);
+                if (bj.valid && RTPN_SCHECK_ID(bj.c >= 0 && bj.c < a.nc && (bj.emap + 1) * EQ <= L::NL, 101, bj.c)) {
+                    const CUtensorMap* mp = bj.target ? a.tmap + bj.emap : maps + bj.kind * L::NMAP + bj.emap;
+                    tma_load_4d(smem_addr(buf + bj.dst), mp, bj.x, bj.y, bj.z, bj.c, full);
                 }
-            } else {
-                const int t = j / NK, k = j % NK;
-                if (t < nt) {
-                    const int c = cB0 + offB_s + t * len;  // first component of the run
-                    const unsigned d = smem_addr(buf + L::SRCO + t * L::SRC_T + k * L::REG);
-                    const CUtensorMap* mp = maps + (ebox / EQ - 1);
-                    if (RTPN_SCHECK_ID(c >= 0 && c < a.nc && ebox <= L::NL, 101, c)) {
-                        if (k < TZ) {               // tile plane z0 + k
-                            tma_load_4d(d, mp + MAP_PLANE * L::NMAP, g.x0, g.y0, g.z0 + k, c, full);
-                        } else if (k == L::KY) {    // cos-type sources are read at y+1, sin-type at y-1
-                            tma_load_4d(d, mp + MAP_YROW * L::NMAP, g.x0, t == 0 ? g.hc[1][1] : g.hc[1][0], g.z0, c,
-                                        full);
-                        } else if (k == L::KZ) {    // z slot 1 (l + M even) is read at z+1
-                            tma_load_4d(d, mp + MAP_PLANE * L::NMAP, g.x0, g.y0,
-                                        ((B + i) & 1) == 0 ? g.hc[2][1] : g.hc[2][0], c, full);
-                        } else {                    // x slot 1 is read at x+1 (upper halo group)
-                            tma_load_4d(d, mp + MAP_XGRP * L::NMAP, dir_x(i, t) > 0 ? g.hx_start[1] : g.hx_start[0],
-                                        g.y0, g.z0, c, full);
-                        }
-                    }
-                }
-            }
+            });
+            if (runs.nt > 0)
+                bulk_load(smem_addr(buf + L::COEFO), a.coefcol + (long long)i * (2 * L::NLC * CPAD), L::COEF_COL,
+                          full);
         }
-        if (lane == 0 && nt > 0)
-            bulk_load(smem_addr(buf + L::COEFO), a.coefcol + (long long)i * (2 * L::NLC * CPAD), L::COEF_COL,
-                      full);
+        __syncwarp();
     }
     if (failed && lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
     // before the CTA ends, the copies of the last stages issued must have landed
     const int first = s > NB ? s - NB : 0;
     for (int r = first; r < s; ++r)
         if (r != a.skip_stage) wait_phase(full0 + 8 * (r % NB), (unsigned)((r / NB) & 1), a.wait_limit);
+}
+
+// ---------------------------------------------------------------- the consumers' column work
+// Byte offsets in a stage buffer of a consumer thread's operands, fixed per tile: its own-type
+// source, the other type's source and its y partner, and per parity p of the source column the
+// x and z partners.  Thread (T, cell (lx, ly, lz)) finishes the targets of type T of its cell.
+struct Operands {
+    int c, o, y, x0, x1, z0, z1;
+};
+
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ>
+RTPN_HD Operands operand_offsets(const TileGeo& g, int T, int lx, int ly, int lz) {
+    using L = Layout<N, A, S, TX, TY, TZ, NB, EQ>;
+    constexpr int B = 1 - A, ES = L::ES, REG = L::REG;
+    const int cp = (ly * TX + lx) * ES;             // the cell in a tile plane region (per component)
+    const int rbo = L::SRCO + T * L::SRC_T;         // own-type sources (z and x partners)
+    const int roo = L::SRCO + (1 - T) * L::SRC_T;   // other-type sources (y partners)
+    const int dy = T == 0 ? -1 : 1;                 // cos-type sources are read at y+1, sin-type at y-1
+    Operands op;
+    op.c = rbo + lz * REG + cp;
+    op.o = roo + lz * REG + cp;
+    op.y = (ly + dy >= 0 && ly + dy < g.wy) ? op.o + dy * TX * ES : roo + L::KY * REG + (lz * TX + lx) * ES;
+    int xo[2], zo[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int dx = dir_x(p, T);
+        xo[p] = (lx + dx >= 0 && lx + dx < g.wx)
+                    ? op.c + dx * ES
+                    : rbo + L::KX * REG + ((lz * L::RY + ly) * L::XW + (dx > 0 ? g.hx_elem[1] : g.hx_elem[0])) * ES;
+        const int dz = ((B + p) & 1) == 0 ? 1 : -1;
+        zo[p] = (lz + dz >= 0 && lz + dz < g.wz) ? op.c + dz * REG : rbo + L::KZ * REG + cp;
+    }
+    op.x0 = xo[0];
+    op.x1 = xo[1];
+    op.z0 = zo[0];
+    op.z1 = zo[1];
+    return op;
+}
+
+// Scatter source column i of a stage buffer into the accumulators of target columns i - 1 (prev),
+// i (cur) and i + 1 (next) of type T: every source value yields its half-grid differences
+// (Section 2.1), each scattered into its <= 10 targets with the column's coupling constants
+// (Eqs. 4-5).  At |m| = 0 only the cos type exists: the absent type's constants are zero (its
+// regions hold earlier, finite data), so the same sweep serves every column.  Sources
+// q = fq .. N/2 (q < fq has l < i: not in the column) are entered at the chunk of kChunk slots
+// holding fq; slots below fq carry zero constants and read finite shared memory.
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ>
+RTPN_HD void sweep_column(const unsigned char* buf, const Operands& op, int T, int i,
+                          float (&prev)[(N - A) / 2 + 1], float (&cur)[(N - A) / 2 + 1],
+                          float (&next)[(N - A) / 2 + 1]) {
+    using L = Layout<N, A, S, TX, TY, TZ, NB, EQ>;
+    constexpr int B = 1 - A, UB = L::UB;
+    constexpr int NLA = (N - A) / 2 + 1, NLB = (N - B) / 2 + 1;
+    const int fq = first_l(i, B) / 2;  // run slot of source q is q - fq
+    const int sh = -fq * UB;           // so source q sits at q * UB from each base
+    const unsigned char* pc = buf + op.c + sh;
+    const unsigned char* px = buf + ((i & 1) ? op.x1 : op.x0) + sh;
+    const unsigned char* pz = buf + ((i & 1) ? op.z1 : op.z0) + sh;
+    const unsigned char* po = buf + op.o + sh;
+    const unsigned char* py = buf + op.y + sh;
+    const float* cf = reinterpret_cast<const float*>(buf + L::COEFO);
+    const float4* kown = reinterpret_cast<const float4*>(cf + T * L::NLC * CPAD);
+    const float4* koth = reinterpret_cast<const float4*>(cf + (1 - T) * L::NLC * CPAD);
+    auto slot = [&](auto qi) {
+        constexpr int q = decltype(qi)::value;
+        if constexpr (q < NLB) {
+            constexpr int ls = 2 * q + B;
+            constexpr int lm = (ls - 1) / 2, lp = (ls + 1) / 2;  // acc index of l-1, l+1
+            constexpr bool has_m = ls - 1 >= 0 && lm < NLA;
+            constexpr bool has_p = ls + 1 <= N && lp < NLA;
+            if constexpr (has_m || has_p) {
+                constexpr int am = has_m ? lm : 0, ap = has_p ? lp : 0;
+                const float c = lds<S>(pc, q * UB);
+                const float ddx = lds<S>(px, q * UB) - c;
+                const float ddz = lds<S>(pz, q * UB) - c;
+                RTPN_CHECK_PTR(kown + 3 * q + 1);
+                const float4 k0 = kown[3 * q], k1 = kown[3 * q + 1];
+                const float co = lds<S>(po, q * UB);
+                const float ddy = lds<S>(py, q * UB) - co;
+                RTPN_CHECK_PTR(koth + 3 * q + 2);
+                const float4 k2 = koth[3 * q + 2];
+                if constexpr (has_m) cur[am] = fmaf(k0.x, ddz, cur[am]);
+                if constexpr (has_p) cur[ap] = fmaf(k0.y, ddz, cur[ap]);
+                if constexpr (has_m) prev[am] = fmaf(k0.z, ddx, prev[am]);
+                if constexpr (has_p) prev[ap] = fmaf(k0.w, ddx, prev[ap]);
+                if constexpr (has_m) next[am] = fmaf(k1.x, ddx, next[am]);
+                if constexpr (has_p) next[ap] = fmaf(k1.y, ddx, next[ap]);
+                if constexpr (has_m) prev[am] = fmaf(k2.x, ddy, prev[am]);
+                if constexpr (has_p) prev[ap] = fmaf(k2.y, ddy, prev[ap]);
+                if constexpr (has_m) next[am] = fmaf(k2.z, ddy, next[am]);
+                if constexpr (has_p) next[ap] = fmaf(k2.w, ddy, next[ap]);
+            }
+        }
+    };
+    auto chunk = [&](auto ci) {
+        constexpr int C = decltype(ci)::value;
+        static_for<kChunk>([&](auto ki) { slot(std::integral_constant<int, C * kChunk + decltype(ki)::value>{}); });
+    };
+    switch (fq / kChunk) { RTPN_CHUNK_CASES(chunk) }
+}
+
+// Finish target column M of type T (accumulators in prev) from its old values in the stage's
+// target planes (at byte offset tgo for this cell) into global memory: FORWARD by Eq. (5),
+// u' = alpha u - beta acc (the u_0 factors al0, be0, ga0 for slot 0 of column 0, cos type, class 0);
+// ADJ_SOURCES lam' = lam + acc / h.  tp: component q = 0 of the run at this cell, components V
+// apart; only an active cell is stored.
+template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ, int MODE>
+RTPN_HD void finish_column(const unsigned char* buf, int tgo, int M, int T, S* tp, long long V, bool active,
+                           float alpha, float beta, float al0, float be0, float ga0, float inv_h,
+                           const float (&prev)[(N - A) / 2 + 1]) {
+    using L = Layout<N, A, S, TX, TY, TZ, NB, EQ>;
+    constexpr int UB = L::UB, NLA = (N - A) / 2 + 1;
+    const bool u0 = A == 0 && M == 0 && T == 0;
+    const int q0 = first_l(M, A) / 2;  // targets q = q0 .. NLA - 1 (l >= M)
+    const unsigned char* ob = buf + tgo - q0 * UB;
+    auto tslot = [&](auto qi) {
+        constexpr int q = decltype(qi)::value;
+        if constexpr (q < NLA) {
+            const float old = lds<S>(ob, q * UB);
+            float nv;
+            if constexpr (MODE == ADJ_SOURCES)
+                nv = fmaf(inv_h, prev[q], old);
+            else if (q == 0)
+                nv = u0 ? fmaf(al0, old, fmaf(-be0, prev[q], ga0)) : fmaf(alpha, old, -beta * prev[q]);
+            else
+                nv = fmaf(alpha, old, -beta * prev[q]);
+            if (active) win::store<S>(tp + (long long)q * V, nv);
+        }
+    };
+    switch (q0) { RTPN_SLOT_CASES(tslot) }
 }
 
 template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ, int MODE>
@@ -439,7 +663,6 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     static_assert((N + 2) / 2 <= kMaxSlots, "slot switch covers N <= 45");
     constexpr int B = 1 - A;
     constexpr int NLA = (N - A) / 2 + 1;   // class-A components of a run, at most
-    constexpr int NLB = (N - B) / 2 + 1;   // class-B components of a run, at most
     constexpr int CELLS = L::CELLS;
     constexpr int UB = L::UB, REG = L::REG, ES = L::ES;
     constexpr int NST = N + 2;  // stage i: sources of column i (i <= N), targets of column i - 1
@@ -480,12 +703,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     // the same code: the type only selects regions, coupling-constant rows and the y direction.
     const int T = tid / CELLS, ctid = tid % CELLS;
     const int lx = ctid % TX, ly = (ctid / TX) % TY, lz = ctid / (TX * TY);
-    const int cp = (ly * TX + lx) * ES;  // the cell in a tile plane region (per component)
-    const int rbo = L::SRCO + T * L::SRC_T;         // own-type sources (z and x partners)
-    const int roo = L::SRCO + (1 - T) * L::SRC_T;   // other-type sources (y partners)
-    const int dy = T == 0 ? -1 : 1;                 // cos-type sources are read at y+1, sin-type at y-1
-    const int cown = T * L::NLC * CPAD, coth = (1 - T) * L::NLC * CPAD;  // coupling-constant rows (floats)
-    const int tgo = L::TGTO + T * L::TGT_T + lz * REG + cp;              // this cell's old target values
+    const int tgo = L::TGTO + T * L::TGT_T + lz * REG + (ly * TX + lx) * ES;  // this cell's old target values
 
     // the three live target columns; their roles (prev, cur, next) rotate by one per stage
     float wa[NLA], wb[NLA], wc[NLA];
@@ -493,9 +711,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     TileGeo g{};
     bool active = false;
     long long cell = 0;
-    // byte offsets in a stage buffer, fixed per tile: the own source, the other type's source and
-    // its y partner, and per parity p of the source column the x and z partners
-    int off_c = 0, off_o = 0, off_y = 0, off_x0 = 0, off_x1 = 0, off_z0 = 0, off_z1 = 0;
+    Operands op{};                                     // operand offsets, fixed per tile
     float alE = 0.f, beE = 0.f, alO = 0.f, beO = 0.f;  // Eq. (5) factors of columns M even / odd
     float al0 = 0.f, be0 = 0.f, ga0 = 0.f;             // u_0 (class 0, type 0 only)
     // ADJ_TARGETS: factor derivatives, the u_0 source, the multipliers of the target column being
@@ -522,23 +738,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
             g = tile_geo<TX, TY, TZ, L::G>(a, tile);
             active = lx < g.wx && ly < g.wy && lz < g.wz;
             cell = ((long long)(g.z0 + lz) * a.ny + (g.y0 + ly)) * a.nx + (g.x0 + lx);
-            off_c = rbo + lz * REG + cp;
-            off_o = roo + lz * REG + cp;
-            off_y = (ly + dy >= 0 && ly + dy < g.wy) ? off_o + dy * TX * ES : roo + L::KY * REG + (lz * TX + lx) * ES;
-            auto xoff = [&](int p) {
-                const int dx = dir_x(p, T);
-                return (lx + dx >= 0 && lx + dx < g.wx)
-                           ? off_c + dx * ES
-                           : rbo + L::KX * REG + ((lz * L::RY + ly) * L::XW + (dx > 0 ? g.hx_elem[1] : g.hx_elem[0])) * ES;
-            };
-            auto zoff = [&](int p) {
-                const int dz = ((B + p) & 1) == 0 ? 1 : -1;
-                return (lz + dz >= 0 && lz + dz < g.wz) ? off_c + dz * REG : rbo + L::KZ * REG + cp;
-            };
-            off_x0 = xoff(0);
-            off_x1 = xoff(1);
-            off_z0 = zoff(0);
-            off_z1 = zoff(1);
+            op = operand_offsets<N, A, S, TX, TY, TZ, NB, EQ>(g, T, lx, ly, lz);
 #pragma unroll
             for (int q = 0; q < NLA; ++q) prev[q] = cur[q] = next[q] = 0.f;
             if (MODE != ADJ_SOURCES && active) {  // the transposed coupling uses no factors
@@ -604,76 +804,24 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
         }
         const unsigned char* buf = bufs + b * L::BUF;
 
-        if (column_len(N, i, B) > 0) {
-            // ---- scatter source column i into prev (i-1), cur (i), next (i+1).  At |m| = 0 only the
-            // cos type exists: the absent type's constants are zero (its regions hold earlier, finite
-            // data), so the same sweep serves every column.
-            const int fq = first_l(i, B) / 2;  // run slot of source q is q - fq
-            const int sh = -fq * UB;           // so source q sits at q * UB from each base
-            const unsigned char* pc = buf + off_c + sh;
-            const unsigned char* px = buf + ((i & 1) ? off_x1 : off_x0) + sh;
-            const unsigned char* pz = buf + ((i & 1) ? off_z1 : off_z0) + sh;
-            const unsigned char* po = buf + off_o + sh;
-            const unsigned char* py = buf + off_y + sh;
-            const float* cf = reinterpret_cast<const float*>(buf + L::COEFO);
-            const float4* kown = reinterpret_cast<const float4*>(cf + cown);
-            const float4* koth = reinterpret_cast<const float4*>(cf + coth);
-            // sources q = fq .. NLB - 1 (q < fq has l < i: not in the column)
-            auto slot = [&](auto qi) {
-                constexpr int q = decltype(qi)::value;
-                if constexpr (q < NLB) {
-                    constexpr int ls = 2 * q + B;
-                    constexpr int lm = (ls - 1) / 2, lp = (ls + 1) / 2;  // acc index of l-1, l+1
-                    constexpr bool has_m = ls - 1 >= 0 && lm < NLA;
-                    constexpr bool has_p = ls + 1 <= N && lp < NLA;
-                    if constexpr (has_m || has_p) {
-                        if (!RTPN_SCHECK(q - fq >= -(kChunk - 1) && q - fq < column_len(N, i, B))) return;
-                        constexpr int am = has_m ? lm : 0, ap = has_p ? lp : 0;
-                        const float c = lds<S>(pc, q * UB);
-                        const float ddx = lds<S>(px, q * UB) - c;
-                        const float ddz = lds<S>(pz, q * UB) - c;
-                        const float4 k0 = kown[3 * q], k1 = kown[3 * q + 1];
-                        const float co = lds<S>(po, q * UB);
-                        const float ddy = lds<S>(py, q * UB) - co;
-                        const float4 k2 = koth[3 * q + 2];
-                        if constexpr (has_m) cur[am] = fmaf(k0.x, ddz, cur[am]);
-                        if constexpr (has_p) cur[ap] = fmaf(k0.y, ddz, cur[ap]);
-                        if constexpr (has_m) prev[am] = fmaf(k0.z, ddx, prev[am]);
-                        if constexpr (has_p) prev[ap] = fmaf(k0.w, ddx, prev[ap]);
-                        if constexpr (has_m) next[am] = fmaf(k1.x, ddx, next[am]);
-                        if constexpr (has_p) next[ap] = fmaf(k1.y, ddx, next[ap]);
-                        if constexpr (has_m) prev[am] = fmaf(k2.x, ddy, prev[am]);
-                        if constexpr (has_p) prev[ap] = fmaf(k2.y, ddy, prev[ap]);
-                        if constexpr (has_m) next[am] = fmaf(k2.z, ddy, next[am]);
-                        if constexpr (has_p) next[ap] = fmaf(k2.w, ddy, next[ap]);
-                    }
-                }
-            };
-            // chunks of kChunk slots from the one holding fq; slots below fq carry zero coupling
-            // constants and read finite (zeroed or earlier) shared memory
-            auto chunk = [&](auto ci) {
-                constexpr int C = decltype(ci)::value;
-                static_for<kChunk>([&](auto ki) { slot(std::integral_constant<int, C * kChunk + decltype(ki)::value>{}); });
-            };
-            switch (fq / kChunk) { RTPN_CHUNK_CASES(chunk) }
-        }
+        if (column_len(N, i, B) > 0) sweep_column<N, A, S, TX, TY, TZ, NB, EQ>(buf, op, T, i, prev, cur, next);
         if (finw) {
-            // ---- finish target column M = i - 1 (its accumulators are in prev), Eq. (5); the old
-            // values are the column's tile plane boxes in this stage
             const int M = i - 1;
             const float alpha = (M & 1) ? alO : alE, beta = (M & 1) ? beO : beE;
-            // u_0 (class 0, l = 0: slot 0 of column 0, cos type) takes its own factors and source
-            const bool u0 = A == 0 && M == 0 && T == 0;
-            S* tp = reinterpret_cast<S*>(a.tgt) +
-                    (long long)(cA0 + offA + T * column_len(N, M, A) - first_l(M, A) / 2) * V + cell;
+            const int q0 = first_l(M, A) / 2;
             (void)RTPN_SCHECK(offA == colA[M]);
-            const int q0 = first_l(M, A) / 2;  // targets q = q0 .. NLA - 1 (l >= M)
-            const unsigned char* ob = buf + tgo - q0 * UB;
-            auto tslot = [&](auto qi) {
-                constexpr int q = decltype(qi)::value;
-                if constexpr (q < NLA) {
-                    const float old = lds<S>(ob, q * UB);
-                    if constexpr (MODE == ADJ_TARGETS) {
+            if constexpr (MODE != ADJ_TARGETS) {
+                S* tp = reinterpret_cast<S*>(a.tgt) + (long long)(cA0 + offA + T * column_len(N, M, A) - q0) * V + cell;
+                finish_column<N, A, S, TX, TY, TZ, NB, EQ, MODE>(buf, tgo, M, T, tp, V, active, alpha, beta, al0, be0,
+                                                                 ga0, a.inv_h, prev);
+            } else {
+                // ---- the pull-back through the substep on class A (see ADJ_TARGETS above)
+                const bool u0 = A == 0 && M == 0 && T == 0;
+                const unsigned char* ob = buf + tgo - q0 * UB;
+                auto tslot = [&](auto qi) {
+                    constexpr int q = decltype(qi)::value;
+                    if constexpr (q < NLA) {
+                        const float old = lds<S>(ob, q * UB);
                         const float la = lpre[q];
                         const float r = -a.inv_h * prev[q];  // the forward residual (without q)
                         const long long loc = (long long)(offA + T * column_len(N, M, A) - q0 + q) * V + cell;
@@ -697,19 +845,10 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                             a.wout[loc] = be * la;
                             a.lam[(long long)cA0 * V + loc] = al * la;
                         }
-                    } else {
-                        float nv;
-                        if constexpr (MODE == ADJ_SOURCES)
-                            nv = fmaf(a.inv_h, prev[q], old);
-                        else if (q == 0)
-                            nv = u0 ? fmaf(al0, old, fmaf(-be0, prev[q], ga0)) : fmaf(alpha, old, -beta * prev[q]);
-                        else
-                            nv = fmaf(alpha, old, -beta * prev[q]);
-                        if (active) win::store<S>(tp + (long long)q * V, nv);
                     }
-                }
-            };
-            switch (q0) { RTPN_SLOT_CASES(tslot) }
+                };
+                switch (q0) { RTPN_SLOT_CASES(tslot) }
+            }
         }
         // the stage buffer is free once every lane of the warp is past its reads
         __syncwarp();

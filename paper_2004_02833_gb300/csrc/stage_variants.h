@@ -4,4 +4,4 @@
 // first listed variant that fits and whose width divides nx.  At most one entry per (order, tile,
 // depth).  The build reads this list: keep it a single line of X(...) entries.
 #pragma once
-#define RTPN_STAGE_VARIANTS(X) X(39, 40, 2, 2, 2, 1) X(39, 40, 2, 2, 4, 1) X(39, 32, 2, 2, 3, 1) X(29, 32, 2, 2, 3, 1) X(29, 40, 2, 2, 2, 1) X(19, 32, 2, 2, 3, 1) X(19, 40, 2, 2, 2, 1) X(15, 32, 2, 2, 3, 1) X(15, 32, 2, 2, 4, 1) X(15, 48, 2, 2, 4, 1) X(15, 64, 2, 2, 3, 1) X(7, 32, 2, 2, 4, 1)
+#define RTPN_STAGE_VARIANTS(X) X(39, 40, 2, 2, 2, 1) X(39, 40, 2, 2, 4, 1) X(39, 32, 2, 2, 3, 1) X(29, 32, 2, 2, 3, 1) X(29, 40, 2, 2, 2, 1) X(19, 32, 2, 2, 3, 1) X(19, 40, 2, 2, 2, 1) X(15, 32, 3, 3, 3, 1) X(15, 32, 2, 2, 3, 1) X(15, 32, 2, 2, 4, 1) X(15, 16, 4, 4, 4, 1) X(15, 48, 2, 2, 4, 1) X(15, 64, 2, 2, 3, 1) X(7, 32, 2, 2, 4, 1)

@@ -8,9 +8,11 @@ Tolerances:
     merged schedule of the library, each pass's class rounded to BF16 after it is written).  The
     GPU applies the same roundings and differs from the model only where its FP32 arithmetic tips
     a rounding the other way (about 2^-16 of the roundings, one BF16 ulp each, propagated by a
-    non-expansive step), so its L2 distance to the model must stay below a tenth of the model's
-    own L2 distance to the exact (FP64) result: the BF16 path adds nothing beyond storage
-    rounding.  The size of that rounding error itself is a measured result, not a pass/fail bound.
+    non-expansive step), so over a few steps its L2 distance to the model must stay below a tenth
+    of the model's own L2 distance to the exact (FP64) result: the BF16 path adds nothing beyond
+    storage rounding.  Over long runs the two rounded trajectories decorrelate (see
+    ``BF16_STRICT_STEPS``) and the GPU's BF16 error must be at most twice the model's.  The size of
+    that rounding error itself is a measured result, not a pass/fail bound.
 """
 import numpy as np
 import pytest
@@ -68,7 +70,19 @@ def assert_parity(got, ref, precision, P=None, u0=None, k=None):
     model = bf16_model(P, u0, k)
     dev = float(np.linalg.norm(got - model))
     eff = float(np.linalg.norm(model - ref))
-    assert dev <= 0.1 * eff, ("bf16", dev / max(eff, 1e-300), rel_err(got, ref))
+    if k <= BF16_STRICT_STEPS:
+        assert dev <= 0.1 * eff, ("bf16", dev / max(eff, 1e-300), rel_err(got, ref))
+    else:
+        err = float(np.linalg.norm(got - ref))
+        assert err <= 2.0 * eff, ("bf16", err / max(eff, 1e-300), rel_err(got, ref))
+
+
+# Up to this many steps the GPU's BF16 state follows the rounding model to a tenth of the rounding
+# effect.  Over longer runs a rounding that the FP32 arithmetic tips the other way changes the
+# next roundings of that entry and of its stencil neighbours, and the two rounded trajectories
+# decorrelate (a 100-step P39 run measured their distance at 1.2 times the rounding effect).  From
+# there on the check is that the GPU's BF16 error is no larger than twice the model's.
+BF16_STRICT_STEPS = 5
 
 
 def rel_err(got, ref):
@@ -281,6 +295,12 @@ STAGE_CASES = [
     # more tiles than CTAs (one per SM): CTAs walk several tiles, partial ones among them
     (7, (12, 44, 72), "vacuum", (32, 2, 2), 4),
     (15, (9, 30, 72), "periodic", (32, 2, 2), 4),
+    # three rows and planes per tile (partial in y and z), two CTAs per SM
+    (15, (7, 10, 64), "periodic", (32, 3, 3), 3),
+    (15, (11, 8, 40), "vacuum", (32, 2, 2), 3),
+    # the showcase's middle orders
+    (19, (6, 7, 64), "vacuum", (32, 2, 2), 3),
+    (29, (5, 6, 40), "periodic", (40, 2, 2), 2),
 ]
 
 
@@ -300,6 +320,27 @@ def test_stage_kernel(cuda_device, coupling_cache, N, shape, bc, tile, depth, pr
         ctx.step(3)
         got = ctx.get_moments()
     assert_parity(got, ref, precision, P, u0, 3)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "vacuum"])
+def test_stage_fp32_only_tile(cuda_device, coupling_cache, bc):
+    # P15 16x4x4: 16 columns leave no 16-byte x halo group with four rows in BF16, so the variant is
+    # compiled for FP32 only; BF16 storage refuses it
+    inst, u0 = synth.random_instance(15, (9, 7, 48), seed=316, bc=bc)
+    P = oracle_problem(inst, coupling_cache)
+    ref = P.run(u0, 3)
+    with rtpn.Context(15, inst.shape, inst.h, inst.bc, "bf16", inst.dt) as ctx:
+        with pytest.raises(rtpn.RtpnError) as e:
+            ctx.set_kernel("stage", (16, 4, 4), 4)
+        assert e.value.code == rtpn.EUNSUPPORTED
+    with rtpn.Context(15, inst.shape, inst.h, inst.bc, "fp32", inst.dt) as ctx:
+        ctx.set_kernel("stage", (16, 4, 4), 4)
+        assert ctx.info().kernel == 3 and tuple(ctx.info().tile) == (16, 4, 4)
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        ctx.step(3)
+        got = ctx.get_moments()
+    assert_parity(got, ref, "fp32")
 
 
 def test_stage_depth_that_fits_bf16_only(cuda_device, coupling_cache):
@@ -453,7 +494,8 @@ def test_media_and_source_changed_between_steps(cuda_device, coupling_cache, N, 
 @pytest.mark.parametrize("N", [19, 29])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_generic_kernel_at_orders_without_compiled_kernels(cuda_device, coupling_cache, N, precision):
-    # P19 and P29 (the reactor showcase's middle orders) run on the generic kernel
+    # P19 and P29 (the reactor showcase's middle orders) on a grid whose nx is no multiple of the
+    # 16-byte group: the staged variants do not apply, the generic kernel runs
     inst, u0 = synth.random_instance(N, (3, 4, 5), seed=900 + N, bc="vacuum")
     ref = oracle_problem(inst, coupling_cache).run(u0, 2)
     with rtpn.Context(N, inst.shape, inst.h, inst.bc, precision, inst.dt) as ctx:
@@ -463,6 +505,24 @@ def test_generic_kernel_at_orders_without_compiled_kernels(cuda_device, coupling
         ctx.step(2)
         got = ctx.get_moments()
     assert rel_err(got, ref) <= TOL[precision], rel_err(got, ref)
+
+
+@pytest.mark.parametrize("N,precision", [(7, "fp64"), (7, "fp32"), (19, "fp32")])
+def test_reactor_media_vs_oracle(cuda_device, coupling_cache, N, precision):
+    # the showcase's media (vacuum walls, absorbing shell and water, source rods with no absorption)
+    # on a small cube, from a zero state, against the oracle; P19 on its staged variant
+    inst = synth.reactor_like(N, 24 if N == 7 else 16)
+    P = oracle_problem(inst, coupling_cache)
+    ref = P.run(inst.full_state(), 6)
+    assert np.abs(ref[0]).max() > 0
+    with rtpn.Context(N, inst.shape, inst.h, inst.bc, precision, inst.dt) as ctx:
+        if N == 19:
+            ctx.set_kernel("stage")
+            assert ctx.info().kernel == 3
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.step(6)
+        got = ctx.get_moments()
+    assert_parity(got, ref, precision)
 
 
 def test_reactor_showcase_converges_in_N(cuda_device):
