@@ -72,7 +72,7 @@ def peaks():
 # capture time: once any of them changes, the traffic is reported as null.  `--record-traffic`
 # writes the file from the capture's CSV.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stage_traffic.json")
-KERNEL_SOURCES = ["stage_impl.cuh", "stage.cu", "kernels_stage.cu", "stage_variants.h", "window_impl.cuh"]
+KERNEL_SOURCES = ["stage_impl.cuh", "stage.cu", "kernels_stage.cu", "window_impl.cuh"]
 
 
 def kernel_source_hash() -> str:

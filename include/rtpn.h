@@ -217,6 +217,18 @@ int rtpn_step(rtpn_ctx* ctx, int k);
  */
 int rtpn_substep(rtpn_ctx* ctx, int cls, int half);
 
+/*
+ * Halo exchange between the blocks of a decomposed domain (Section 3: each block of the
+ * block-structured grid keeps one halo layer per face, refreshed from its neighbours between the
+ * sweeps).  Copies z-planes [src_z, src_z + nz) of every component of class cls (0 even, 1 odd,
+ * -1 both) from src's state into planes [dst_z, dst_z + nz) of dst's, device to device in one
+ * strided copy.  The contexts must share N, precision, nx and ny (and the device); the planes must
+ * lie inside both grids and not overlap within one context.  Ordered on dst's stream after the work
+ * queued on src's stream, and src's later work waits for it (when the streams differ).
+ * Asynchronous; RTPN_EINVAL on a mismatch or out-of-range planes.
+ */
+int rtpn_copy_planes(rtpn_ctx* dst, int dst_z, rtpn_ctx* src, int src_z, int nz, int cls);
+
 /* Sum of u_0 over all cells, accumulated in FP64 in a fixed order (deterministic).
  * Writes the host double *out; synchronises. */
 int rtpn_sum_u0(rtpn_ctx* ctx, double* out);

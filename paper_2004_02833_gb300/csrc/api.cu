@@ -806,6 +806,39 @@ int rtpn_substep(rtpn_ctx* ctx, int cls, int half) {
     return run_pass(ctx, cls, half ? FAC_HALF : FAC_FULL, ctx->stream);
 }
 
+int rtpn_copy_planes(rtpn_ctx* dst, int dst_z, rtpn_ctx* src, int src_z, int nz, int cls) {
+    if (!dst || !src || nz < 0 || cls < -1 || cls > 1) return RTPN_EINVAL;
+    if (src->N != dst->N || src->prec != dst->prec || src->g.nx != dst->g.nx || src->g.ny != dst->g.ny)
+        return fail(dst, RTPN_EINVAL, "copy_planes: the contexts differ in order, precision, nx or ny");
+    if (src_z < 0 || dst_z < 0 || src_z + nz > src->g.nz || dst_z + nz > dst->g.nz)
+        return fail(dst, RTPN_EINVAL, "copy_planes: planes outside a grid");
+    if (src == dst && nz > 0 && src_z < dst_z + nz && dst_z < src_z + nz)
+        return fail(dst, RTPN_EINVAL, "copy_planes: overlapping planes of one context");
+    if (nz == 0) return RTPN_OK;
+    // the components of a class are contiguous in the internal order (class 0 first)
+    const int c0 = cls == 1 ? dst->md.ne : 0;
+    const int n = cls == -1 ? dst->md.nc : (cls == 0 ? dst->md.ne : dst->md.no);
+    const size_t plane = (size_t)dst->g.nx * dst->g.ny * dst->elem;
+    const char* sp = (const char*)src->u + ((size_t)c0 * src->g.V + (size_t)src_z * dst->g.nx * dst->g.ny) * dst->elem;
+    char* dp = (char*)dst->u + ((size_t)c0 * dst->g.V + (size_t)dst_z * dst->g.nx * dst->g.ny) * dst->elem;
+    // the copy runs on dst's stream after src's queued work, and src's later work runs after it
+    cudaEvent_t ev = nullptr;
+    if (src->stream != dst->stream) {
+        CUDA_TRY(dst, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CUDA_TRY(dst, cudaEventRecord(ev, src->stream));
+        CUDA_TRY(dst, cudaStreamWaitEvent(dst->stream, ev, 0));
+    }
+    cudaError_t e = cudaMemcpy2DAsync(dp, (size_t)dst->g.V * dst->elem, sp, (size_t)src->g.V * dst->elem,
+                                      (size_t)nz * plane, (size_t)n, cudaMemcpyDeviceToDevice, dst->stream);
+    if (ev) {
+        if (e == cudaSuccess) e = cudaEventRecord(ev, dst->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(src->stream, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    if (e != cudaSuccess) return fail(dst, RTPN_ECUDA, std::string("copy_planes: ") + cudaGetErrorString(e));
+    return RTPN_OK;
+}
+
 int rtpn_sum_u0(rtpn_ctx* ctx, double* out) {
     if (!ctx || !out) return RTPN_EINVAL;
     const void* u0 = comp_ptr(ctx, ctx->md.internal_of_abi[0]);

@@ -238,3 +238,100 @@ class BlockHalo:
                 u[layer(self.local_n(d) - 1, up_c)] = recv_up
             if recv_lo is not None:
                 u[layer(0, lo_c)] = recv_lo
+
+
+class DeviceSlabs:
+    """The z-slab decomposition on library contexts: one context per slab on the current device,
+    each holding its own planes plus the ghost planes of `SlabHalo`, advanced pass by pass
+    (``Context.substep``) with the ghost planes refreshed device to device after every pass
+    (``Context.copy_planes_from``, rtpn_copy_planes): after a pass on class A, each face's ghost
+    receives the neighbour's outermost own plane of class A, which the next pass (on the other
+    class) reads.  The passes follow the library's merged schedule of Eq. (6), so the slabs
+    together take the same steps as one context over the whole grid.  The values a context
+    computes on its own ghost planes are never used: the exchange overwrites them first.
+
+    On one GPU this is the exchange pattern of the multi-GPU decomposition with the transport a
+    device copy; across GPUs the same planes travel by point-to-point sends (``SlabHalo``).
+    """
+
+    def __init__(self, N: int, shape, h: float, bc: str, precision: str, dt: float, slabs_: int,
+                 kernel: str = "auto"):
+        nz, ny, nx = shape
+        self.shape = tuple(shape)
+        self.periodic = bc == "periodic"
+        self.halos = [SlabHalo(N, nz, r, slabs_, self.periodic) for r in range(slabs_)]
+        self.ctx = []
+        for hl in self.halos:
+            c = rtpn.Context(N, (hl.local_nz, ny, nx), h, bc, precision, dt)
+            if kernel != "auto":
+                c.set_kernel(kernel)
+            self.ctx.append(c)
+
+    def close(self):
+        for c in self.ctx:
+            c.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        for c in self.ctx:
+            c.set_stream(stream)
+
+    def set_media(self, sigma_a, sigma_s, q):
+        """Per-cell media of the whole grid [z][y][x] (host arrays); each slab takes its planes,
+        ghosts included."""
+        for hl, c in zip(self.halos, self.ctx):
+            zs = hl.global_planes()
+            c.set_media(sigma_a[zs], sigma_s[zs], q[zs])
+
+    def set_moments(self, u):
+        """The whole state [c][z][y][x] (interface order, host array); ghosts included."""
+        for hl, c in zip(self.halos, self.ctx):
+            c.set_moments(u[:, hl.global_planes()])
+
+    def get_moments(self):
+        """The whole state from the slabs' own planes (host FP64)."""
+        import numpy as np
+
+        out = None
+        for hl, c in zip(self.halos, self.ctx):
+            part = c.get_moments()
+            if out is None:
+                out = np.empty((part.shape[0],) + self.shape)
+            out[:, hl.z0:hl.z1] = part[:, hl.lo:hl.lo + (hl.z1 - hl.z0)]
+        return out
+
+    def _exchange(self, cls: int):
+        for r, hl in enumerate(self.halos):
+            if hl.upper is None:
+                continue
+            up = self.halos[hl.upper]
+            mine, theirs = self.ctx[r], self.ctx[hl.upper]
+            own_top = hl.lo + (hl.z1 - hl.z0) - 1
+            # my highest own plane -> the upper neighbour's lower ghost (local plane 0), and its
+            # lowest own plane -> my upper ghost (my last local plane)
+            theirs.copy_planes_from(mine, own_top, 0, 1, cls)
+            mine.copy_planes_from(theirs, up.lo, hl.local_nz - 1, 1, cls)
+
+    def _pass(self, cls: int, half: bool):
+        for c in self.ctx:
+            c.substep(cls, half)
+        self._exchange(cls)
+
+    def step(self, k: int = 1):
+        """k steps of Eq. (6) in the merged schedule: odd dt/2, then (even dt, odd dt) k - 1 times,
+        even dt, odd dt/2."""
+        if k <= 0:
+            return
+        self._pass(1, True)
+        for s in range(k):
+            self._pass(0, False)
+            self._pass(1, s == k - 1)
+
+    def synchronize(self):
+        for c in self.ctx:
+            c.synchronize()

@@ -63,6 +63,7 @@ SIGNATURES = {
     "rtpn_zero_moments": (_I, [_P]),
     "rtpn_step": (_I, [_P, _I]),
     "rtpn_substep": (_I, [_P, _I, _I]),
+    "rtpn_copy_planes": (_I, [_P, _I, _P, _I, _I, _I]),
     "rtpn_sum_u0": (_I, [_P, ctypes.POINTER(_D)]),
     "rtpn_count_nonfinite": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "rtpn_sum_static": (_I, [_P, _I, ctypes.c_longlong, _P, _P]),
@@ -320,6 +321,11 @@ class Context:
             raise ValueError("out must be a CUDA float64 tensor with at least one element")
         self._chk(lib().rtpn_detector(self._p, ptr, code, where, _P(out.data_ptr()), DEVICE))
         return out
+
+    def copy_planes_from(self, src: "Context", src_z: int, dst_z: int, nz: int, cls: int = -1):
+        """Planes [src_z, src_z + nz) of class cls (-1: both) of src's state into planes
+        [dst_z, dst_z + nz) of this context's (device to device, one strided copy)."""
+        self._chk(lib().rtpn_copy_planes(self._p, int(dst_z), src._p, int(src_z), int(nz), int(cls)))
 
     def sum_u0(self) -> float:
         out = _D()
