@@ -483,18 +483,25 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
         c = rtpn.Context(15, inst.shape, inst.h, inst.bc, "fp32", inst.dt)
         c.set_stream(stream)
         c.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        # warm-up: every kernel of both calls loaded once
+        c.step(2)
+        c.adjoint(w, 1, ckpt_every=1)
+        c.zero_moments()
+        c.synchronize()
         t0 = time.perf_counter()
         c.step(200)
         c.synchronize()
         t_fwd = time.perf_counter() - t0
         c.zero_moments()
+        c.synchronize()
         t0 = time.perf_counter()
         J, _ = c.adjoint(w, 200, ckpt_every=20)
         t_adj = time.perf_counter() - t0
+        kernel = {v: k for k, v in rtpn.KERNEL.items()}.get(c.info().kernel, "?")
         c.close()
         V = inst.shape[0] * inst.shape[1] * inst.shape[2]
         return {"workload": "P15 96^3 checkerboard, vacuum, 200 steps, checkpoints every 20",
-                "J": J, "forward_s": t_fwd, "forward_plus_adjoint_s": t_adj,
+                "kernel": kernel, "J": J, "forward_s": t_fwd, "forward_plus_adjoint_s": t_adj,
                 "cost_ratio_vs_forward": t_adj / t_fwd,
                 "speedup_vs_central_fd": (2 * 3 * V * t_fwd) / t_adj,
                 "note": "central differences of 3 per-cell fields need 2*3*V forward runs"}

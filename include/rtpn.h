@@ -257,18 +257,22 @@ int rtpn_sum_static(const void* x, int dtype, long long n, double* out, void* st
 
 /*
  * Discrete adjoint (gradients of a detector functional).  Starting from the context's current state
- * u(0) and media, runs k steps of Eq. (6) taken literally (odd half, even full, odd half substeps;
- * the schedule the oracle's discrete adjoint transposes) and returns
+ * u(0) and media, runs k steps of Eq. (6) and returns
  *     J = sum over cells of w * u_0(after k steps)          (host double *J)
  * and dJ/dsigma_a, dJ/dsigma_s, dJ/dq per cell ([z][y][x], FP64, host or device per out_where).
  * Each substep u_A' = alpha u_A + beta r_A (Eq. 5) is pulled back exactly: lam_A <- alpha lam_A,
  * lam_B <- lam_B - K^T (beta lam_A) with the transposed staggered stencil, and the media collect
  * lam (dalpha/dc u + dbeta/dc r) at the staggered points, spread to the cells through the
  * transpose of the point mean, plus beta_0 lam_0 for q.  States are checkpointed every ckpt_every
- * steps and each segment is recomputed forward with its pre-substep states kept on the device
- * (device memory ~ (k/ckpt_every + 3 ckpt_every) states).  w is [z][y][x] of dtype at `where`.
- * Afterwards the context holds u(k).  FP64 and FP32 storage (RTPN_EUNSUPPORTED for BF16);
- * RTPN_ESTATE without media; RTPN_ENOMEM if the checkpoints do not fit.  Synchronises.
+ * steps and each segment is recomputed forward before its backward sweep.
+ * Schedules: with the staged kernel active (FP32) every segment runs the merged form of its steps
+ * (odd half pass, even and odd full passes, closing odd half pass: the literal step up to rounding)
+ * with each pass written out of place, device memory ~ (k/ckpt_every + ckpt_every + 4) states;
+ * otherwise the steps are taken literally (odd half, even full, odd half substeps: the schedule
+ * the oracle's discrete adjoint transposes), device memory ~ (k/ckpt_every + 3 ckpt_every + 4)
+ * states.  w is [z][y][x] of dtype at `where`.  Afterwards the context holds u(k).  FP64 and FP32
+ * storage (RTPN_EUNSUPPORTED for BF16); RTPN_ESTATE without media; RTPN_ENOMEM if the states do
+ * not fit; RTPN_ETIMEOUT if a staged kernel's bounded wait ran out.  Synchronises.
  */
 int rtpn_adjoint(rtpn_ctx* ctx, const void* w, int dtype, int where, int k, int ckpt_every,
                  double* g_sa, double* g_ss, double* g_q, int out_where, double* J);

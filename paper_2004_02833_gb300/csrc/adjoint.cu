@@ -12,12 +12,16 @@
 // with dalpha/dc = -tau alpha and dbeta/dc = -tau^2 E'(-c tau), E'(x) = (e^x (x - 1) + 1) / x^2.
 // dJ/dc at the staggered points is spread back to the cells by the transpose of the point mean.
 //
-// The forward is the literal Strang step (odd half, even full, odd half) so that the adjoint is
-// the exact transpose of the computed scheme.  States are checkpointed every `ckpt` steps; each
-// segment is recomputed forward (with the active step kernel) keeping every pre-substep state, then
-// swept backward with the kernels below.  Gradient accumulators are FP64.
+// With the generic kernels (FP64, the parity path) the forward is the literal Strang step (odd half,
+// even full, odd half), so that the adjoint is the exact transpose of the computed scheme.  States
+// are checkpointed every `ckpt` steps; each segment is recomputed forward (with the active step
+// kernel) keeping every pre-substep state, then swept backward with k_adj_targets and
+// k_adj_sources.  FP32 storage on the staged kernel runs the merged form of the step with
+// out-of-place segment states and a cell-by-cell pull-back (adjoint_staged).  Gradient accumulators
+// are FP64.
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -184,6 +188,78 @@ __global__ void k_adj_sources(F* __restrict__ lam, const F* __restrict__ w, Part
             acc += tabT.coef[p] * (other - wa[cell]);
         }
         lam[(long long)(tabT.a0 + t) * g.V + cell] -= acc;
+    }
+}
+
+// The pull-back through a pass on class A between two stored FP32 states, cell by cell.  The pass
+// computed u_A' = alpha u_A + beta r_A (Eq. 5), so its residual is r_A = (u_A' - alpha u_A) / beta
+// (q included for u_0) and no stencil is needed: gacc[slot] += sum_a lam_a (dalpha u_a + dbeta r_a),
+// gq += beta_0 lam_0, w_a = beta_a lam_a.  lam_a <- alpha_a lam_a is left to the next transposed
+// coupling onto class A (the staged ADJ_SOURCES pass scales its targets), which saves a store.
+// Where two passes on class A follow each other (the odd half passes that close one checkpoint
+// segment and open the next), the later one's scaling is still pending when this one is pulled
+// back: pre_ofs >= 0 gives its factors, lam is scaled by them first and stored back.  upre, upost
+// and lam point at class A's first component; w holds class A in its local order.  grp: ngroups x {plane of alpha in
+// the factors (FAC_U0 for u_0), gacc slot, first, end} over idx, the local indices sharing those
+// factors.  One thread per 4 consecutive cells, as float4: V % 4 == 0 (the staged kernel's rows
+// are 16-byte multiples), so every plane starts 16-byte aligned.
+__device__ __forceinline__ float4 ld4_nc(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+__global__ void __launch_bounds__(256) k_adj_pull(const float* __restrict__ upre, const float* __restrict__ upost,
+                                                  float* __restrict__ lam, float* __restrict__ w,
+                                                  const float* __restrict__ fac, const float* __restrict__ dfac,
+                                                  int fac_ofs, int pre_ofs, const int* __restrict__ grp, int ngroups,
+                                                  const int* __restrict__ idx, long long V,
+                                                  double* __restrict__ gacc, double* __restrict__ gq) {
+    const long long c0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c0 >= V) return;
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const int fp = __ldg(grp + 4 * gi), slot = __ldg(grp + 4 * gi + 1);
+        const int jb = __ldg(grp + 4 * gi + 2), je = __ldg(grp + 4 * gi + 3);
+        const bool u0 = fp == FAC_U0;
+        const long long ap = u0 ? FAC_U0 : fp + fac_ofs, dp = u0 ? 32 : fp + fac_ofs;
+        float al[4], be[4], da[4], db[4], ib[4], acc[4] = {0.f, 0.f, 0.f, 0.f}, gqa[4] = {0.f, 0.f, 0.f, 0.f};
+        float pre[4] = {1.f, 1.f, 1.f, 1.f};
+        if (pre_ofs >= 0) {
+            const float4 p4 = ld4_nc(fac + (u0 ? (long long)FAC_U0 : (long long)fp + pre_ofs) * V + c0);
+            pre[0] = p4.x, pre[1] = p4.y, pre[2] = p4.z, pre[3] = p4.w;
+        }
+        {
+            const float4 a4 = ld4_nc(fac + ap * V + c0), b4 = ld4_nc(fac + (ap + 1) * V + c0);
+            const float4 d4 = ld4_nc(dfac + dp * V + c0), e4 = ld4_nc(dfac + (dp + 1) * V + c0);
+            al[0] = a4.x, al[1] = a4.y, al[2] = a4.z, al[3] = a4.w;
+            be[0] = b4.x, be[1] = b4.y, be[2] = b4.z, be[3] = b4.w;
+            da[0] = d4.x, da[1] = d4.y, da[2] = d4.z, da[3] = d4.w;
+            db[0] = e4.x, db[1] = e4.y, db[2] = e4.z, db[3] = e4.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ib[c] = 1.f / be[c];
+#pragma unroll 2
+        for (int j = jb; j < je; ++j) {
+            const long long o = (long long)__ldg(idx + j) * V + c0;
+            const float4 u4 = ld4_nc(upre + o), p4 = ld4_nc(upost + o);
+            float4 l4 = *reinterpret_cast<const float4*>(lam + o);
+            if (pre_ofs >= 0) {
+                l4 = make_float4(pre[0] * l4.x, pre[1] * l4.y, pre[2] * l4.z, pre[3] * l4.w);
+                *reinterpret_cast<float4*>(lam + o) = l4;
+            }
+            const float u[4] = {u4.x, u4.y, u4.z, u4.w}, up[4] = {p4.x, p4.y, p4.z, p4.w};
+            const float la[4] = {l4.x, l4.y, l4.z, l4.w};
+            float wv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float r = fmaf(-al[c], u[c], up[c]) * ib[c];
+                acc[c] = fmaf(la[c], fmaf(da[c], u[c], db[c] * r), acc[c]);
+                gqa[c] = fmaf(be[c], la[c], gqa[c]);
+                wv[c] = be[c] * la[c];
+            }
+            *reinterpret_cast<float4*>(w + o) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            gacc[(long long)slot * V + c0 + c] += (double)acc[c];
+            if (u0) gq[c0 + c] += (double)gqa[c];
+        }
     }
 }
 
@@ -418,19 +494,6 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
     Buf fin;
     if (!fin.alloc(state)) return afail(ctx, RTPN_ENOMEM, "adjoint: final state");
     cudaMemcpyAsync(fin.p, u, state, cudaMemcpyDeviceToDevice, st);
-    // FP32 with the staged kernel: tensor maps over every pre-substep state slot of a segment
-    Buf premaps;
-    size_t mapb = 0;
-    bool staged_targets = false;
-    if constexpr (sizeof(F) == 4 && sizeof(S) == 4) {
-        if (ctx->active_kernel == RTPN_KERNEL_STAGE) {
-            mapb = stage_maps_bytes(ctx);
-            if (!premaps.alloc((size_t)npass * mapb)) return afail(ctx, RTPN_ENOMEM, "adjoint: tensor maps");
-            staged_targets = mapb > 0;
-            for (int p = 0; p < npass && staged_targets; ++p)
-                staged_targets = stage_maps_for(ctx, (char*)seg.p + (size_t)p * state, (char*)premaps.p + (size_t)p * mapb) == 0;
-        }
-    }
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int s0 = sg * ckpt, s1 = std::min(k, s0 + ckpt);
         cudaMemcpyAsync(u, (char*)ck.p + (size_t)sg * state, state, cudaMemcpyDeviceToDevice, st);
@@ -442,32 +505,11 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
             const int cls = (p % 3 == 1) ? 0 : 1;
             const int ofs = (p % 3 == 1) ? FAC_FULL : FAC_HALF;
             const S* pre = (const S*)((char*)seg.p + (size_t)p * state);
-            if (staged_targets) {
-                // the same pull-back on the staged kernel (column sweep over the pre-substep state)
-                const int rc2 = launch_stage_adjoint_targets(ctx, cls, ofs, (const char*)premaps.p + (size_t)p * mapb,
-                                                             (float*)lam.p, (float*)wbuf.p, (const float*)dfac.p,
-                                                             ctx->media + 2 * V, (double*)gacc.p, (double*)gqb.p, st);
-                if (rc2) return afail(ctx, RTPN_ECUDA, "adjoint: staged pull-back failed");
-            } else {
-                k_adj_targets<S, F><<<blocks_for(V, 128), 128, 0, st>>>(pre, (F*)lam.p, (F*)wbuf.p, (const F*)ctx->fac,
-                                                                   (const F*)dfac.p, tf[cls], g, ofs,
-                                                                   ctx->media + 2 * V, (double*)gacc.p,
-                                                                   (double*)gqb.p);
-            }
-            bool staged = false;
-            if constexpr (sizeof(F) == 4) {
-                // the transposed coupling on the staged kernel (same column sweep as a forward pass
-                // on class 1 - cls, sources w, lam += K w / h)
-                if (ctx->active_kernel == RTPN_KERNEL_STAGE) {
-                    const int rc2 = launch_stage_adjoint_sources(ctx, 1 - cls, (float*)lam.p, (const float*)wbuf.p,
-                                                                 std::max(ctx->md.ne, ctx->md.no), st);
-                    if (rc2) return afail(ctx, RTPN_ECUDA, "adjoint: staged transposed coupling failed");
-                    staged = true;
-                }
-            }
-            if (!staged)
-                k_adj_sources<F><<<blocks_for(V, 128), 128, 0, st>>>((F*)lam.p, (const F*)wbuf.p, tt[1 - cls].tab,
-                                                                tf[cls].a0, g);
+            k_adj_targets<S, F><<<blocks_for(V, 128), 128, 0, st>>>(pre, (F*)lam.p, (F*)wbuf.p, (const F*)ctx->fac,
+                                                               (const F*)dfac.p, tf[cls], g, ofs, ctx->media + 2 * V,
+                                                               (double*)gacc.p, (double*)gqb.p);
+            k_adj_sources<F><<<blocks_for(V, 128), 128, 0, st>>>((F*)lam.p, (const F*)wbuf.p, tt[1 - cls].tab,
+                                                            tf[cls].a0, g);
         }
     }
     cudaMemcpyAsync(u, fin.p, state, cudaMemcpyDeviceToDevice, st);
@@ -476,6 +518,151 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return afail(ctx, RTPN_ECUDA, std::string("adjoint: ") + cudaGetErrorString(e));
+    ctx->steps_done += k;
+    return RTPN_OK;
+}
+
+// The class-cls components grouped by the factors they share, for k_adj_pull: {plane of alpha,
+// gacc slot, first, end} per group, then the local indices of every group.
+struct PullTable {
+    std::vector<int> grp, idx;
+};
+PullTable pull_table(const Model& md, int cls) {
+    const int a0 = cls == 0 ? 0 : md.ne, na = cls == 0 ? md.ne : md.no;
+    std::map<int, std::vector<int>> by_plane;
+    for (int t = 0; t < na; ++t) {
+        const int a = md.abi_of_internal[a0 + t];
+        by_plane[a == 0 ? FAC_U0 : 2 * slot_code(md.comp[a].slot)].push_back(t);
+    }
+    PullTable p;
+    for (const auto& [fp, ts] : by_plane) {
+        p.grp.insert(p.grp.end(), {fp, fp == FAC_U0 ? 8 : fp / 2, (int)p.idx.size(), (int)(p.idx.size() + ts.size())});
+        p.idx.insert(p.idx.end(), ts.begin(), ts.end());
+    }
+    return p;
+}
+
+// FP32 storage on the staged kernel.  The k steps run as segments of ckpt whole Strang steps, each in
+// the merged form of the step (odd half pass; even and odd full passes; even full pass; odd half
+// pass): two odd half passes with no even pass between them are one odd full pass in exact
+// arithmetic (alpha_h^2 = alpha, beta_h (1 + alpha_h) = beta), so this is the literal schedule up
+// to rounding.  The passes of a segment write out of place: pass j writes its class into X[j/2 + 1],
+// its old targets come from X[j/2] and its sources from X[(j+1)/2], with X[0] the segment's
+// checkpoint.  Every pass's pre- and post-pass values then stay in memory without copies, and the
+// backward sweep recovers each pass's residual cell by cell (k_adj_pull) instead of re-running its
+// stencil; the transposed coupling runs on the staged kernel (mode ADJ_SOURCES) and also applies
+// the pulled-back class's pending lam <- alpha lam.  The last segment's states are still in place
+// after the forward, so only the earlier ones are recomputed.
+int adjoint_staged(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gsa, double* gss, double* gq_out,
+                   double* J) {
+    const Geom& g = ctx->g;
+    const long long V = g.V;
+    const int nc = ctx->md.nc, ne = ctx->md.ne, no = ctx->md.no;
+    const size_t state = (size_t)nc * V * sizeof(float);
+    cudaStream_t st = ctx->stream;
+    const int nseg = (k + ckpt - 1) / ckpt;
+    const int nring = std::min(k, ckpt) + 1;  // X[1] .. X[m + 1] of the longest segment
+    const size_t mapb = stage_maps_bytes(ctx);
+    if (V % 4 != 0 || mapb == 0) return afail(ctx, RTPN_EUNSUPPORTED, "adjoint: staged kernel layout");
+    Buf ck, ring, lam, wbuf, dfac, gacc, gqb, part, maps, tabs;
+    if (!ck.alloc(state * std::max(nseg, 1)) || !ring.alloc(state * nring) || !lam.alloc(state) ||
+        !wbuf.alloc((size_t)std::max(ne, no) * V * sizeof(float)) ||
+        !dfac.alloc((size_t)DFAC_PLANES * V * sizeof(float)) || !gacc.alloc((size_t)9 * V * sizeof(double)) ||
+        !gqb.alloc((size_t)V * sizeof(double)) || !part.alloc(1024 * sizeof(double)) ||
+        !maps.alloc((size_t)(nseg + nring) * mapb))
+        return afail(ctx, RTPN_ENOMEM, "adjoint: device memory for checkpoints and segment states");
+    auto X = [&](int sg, int i) -> char* {
+        return i == 0 ? (char*)ck.p + (size_t)sg * state : (char*)ring.p + (size_t)(i - 1) * state;
+    };
+    auto XM = [&](int sg, int i) -> const char* {
+        return (const char*)maps.p + (size_t)(i == 0 ? sg : nseg + i - 1) * mapb;
+    };
+    for (int sg = 0; sg < nseg; ++sg)
+        if (stage_maps_for(ctx, X(sg, 0), (char*)maps.p + (size_t)sg * mapb))
+            return afail(ctx, RTPN_ECUDA, "adjoint: tensor maps");
+    for (int i = 1; i <= nring; ++i)
+        if (stage_maps_for(ctx, X(0, i), (char*)maps.p + (size_t)(nseg + i - 1) * mapb))
+            return afail(ctx, RTPN_ECUDA, "adjoint: tensor maps");
+    // the pull-back's component groups of both classes in one device array
+    PullTable pt[2] = {pull_table(ctx->md, 0), pull_table(ctx->md, 1)};
+    std::vector<int> all;
+    size_t at[2][2];
+    for (int c = 0; c < 2; ++c) {
+        at[c][0] = all.size();
+        all.insert(all.end(), pt[c].grp.begin(), pt[c].grp.end());
+        at[c][1] = all.size();
+        all.insert(all.end(), pt[c].idx.begin(), pt[c].idx.end());
+    }
+    if (!tabs.alloc(all.size() * sizeof(int)) ||
+        cudaMemcpy(tabs.p, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return afail(ctx, RTPN_ENOMEM, "adjoint: tables");
+    k_adj_factors<float><<<blocks_for(V), 256, 0, st>>>(ctx->media, ctx->media + V, (float*)dfac.p, g, ctx->dt);
+
+    auto seg_steps = [&](int sg) { return std::min(k, (sg + 1) * ckpt) - sg * ckpt; };
+    auto pass_cls = [](int j) { return (j & 1) ? 0 : 1; };
+    auto pass_ofs = [](int j, int m) { return (j == 0 || j == 2 * m) ? FAC_HALF : FAC_FULL; };
+    auto run_segment = [&](int sg) -> int {
+        const int m = seg_steps(sg);
+        for (int j = 0; j <= 2 * m; ++j) {
+            const int rc = launch_stage_between(ctx, pass_cls(j), pass_ofs(j, m), XM(sg, (j + 1) / 2), XM(sg, j / 2),
+                                                X(sg, j / 2 + 1), st);
+            if (rc) return afail(ctx, RTPN_ECUDA, std::string("adjoint: staged pass: ") +
+                                                      cudaGetErrorString((cudaError_t)rc));
+        }
+        return RTPN_OK;
+    };
+
+    // ---- forward: segment by segment; each end state (even class in X[m], odd class in X[m + 1])
+    // is the next checkpoint, the last one the context's state
+    const size_t even_b = (size_t)ne * V * sizeof(float), odd_b = (size_t)no * V * sizeof(float);
+    if (nseg > 0) cudaMemcpyAsync(X(0, 0), ctx->u, state, cudaMemcpyDeviceToDevice, st);
+    for (int sg = 0; sg < nseg; ++sg) {
+        if (int rc = run_segment(sg)) return rc;
+        const int m = seg_steps(sg);
+        char* dst = sg + 1 < nseg ? X(sg + 1, 0) : (char*)ctx->u;
+        cudaMemcpyAsync(dst, X(sg, m), even_b, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(dst + even_b, X(sg, m + 1) + even_b, odd_b, cudaMemcpyDeviceToDevice, st);
+    }
+    // J = sum w u_0 (u_0 is internal component 0)
+    k_dot_u0<float><<<1024, 256, 0, st>>>((const float*)ctx->u, w_dev, V, (double*)part.p);
+    launch_sum<double>((const double*)part.p, 1024, ctx->partial, 1, ctx->partial + SUM_BLOCKS, st);
+    cudaMemcpyAsync(J, ctx->partial + SUM_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st);
+
+    // ---- backward, pass by pass in reverse
+    float* lp = (float*)lam.p;
+    cudaMemsetAsync(lp, 0, state, st);
+    k_copy_cast<double, float><<<1024, 256, 0, st>>>(w_dev, lp, V);  // lam_0 = w
+    cudaMemsetAsync(gacc.p, 0, (size_t)9 * V * sizeof(double), st);
+    cudaMemsetAsync(gqb.p, 0, (size_t)V * sizeof(double), st);
+    const int* tp = (const int*)tabs.p;
+    // pend[c]: the factor offset of the last pulled-back pass on class c whose lam_c <- alpha lam_c
+    // is still to come (folded into the next transposed coupling onto class c), -1 for none
+    int pend[2] = {-1, -1};
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int m = seg_steps(sg);
+        if (sg < nseg - 1)
+            if (int rc = run_segment(sg)) return rc;
+        for (int j = 2 * m; j >= 0; --j) {
+            const int cls = pass_cls(j), ofs = pass_ofs(j, m);
+            const size_t a0 = cls == 0 ? 0 : (size_t)ne * V;
+            const int ng = (int)pt[cls].grp.size() / 4;
+            const float* pre = (const float*)X(sg, j / 2) + a0;
+            const float* post = (const float*)X(sg, j / 2 + 1) + a0;
+            k_adj_pull<<<blocks_for(V / 4), 256, 0, st>>>(pre, post, lp + a0, (float*)wbuf.p, (const float*)ctx->fac,
+                                                          (const float*)dfac.p, ofs, pend[cls], tp + at[cls][0], ng,
+                                                          tp + at[cls][1], V, (double*)gacc.p, (double*)gqb.p);
+            pend[cls] = ofs;
+            const int rc = launch_stage_adjoint_sources(ctx, 1 - cls, lp, (const float*)wbuf.p, std::max(ne, no),
+                                                        pend[1 - cls], st);
+            if (rc) return afail(ctx, RTPN_ECUDA, "adjoint: staged transposed coupling failed");
+            pend[1 - cls] = -1;
+        }
+    }
+    k_adj_media<<<blocks_for(V), 256, 0, st>>>((const double*)gacc.p, g, gsa, gss);
+    cudaMemcpyAsync(gq_out, gqb.p, (size_t)V * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return afail(ctx, RTPN_ECUDA, std::string("adjoint: ") + cudaGetErrorString(e));
+    if (int rc = rtpn_synchronize(ctx)) return rc;  // also reports a staged wait that ran out
     ctx->steps_done += k;
     return RTPN_OK;
 }
@@ -510,7 +697,9 @@ extern "C" int rtpn_adjoint(rtpn_ctx* ctx, const void* w, int dtype, int where, 
     double* o = (double*)out.p;
     int rc = ctx->prec == RTPN_FP64
                  ? adjoint_impl<double, double>(ctx, (const double*)wd.p, k, ckpt_every, o, o + V, o + 2 * V, J)
-                 : adjoint_impl<float, float>(ctx, (const double*)wd.p, k, ckpt_every, o, o + V, o + 2 * V, J);
+                 : ctx->active_kernel == RTPN_KERNEL_STAGE
+                     ? adjoint_staged(ctx, (const double*)wd.p, k, ckpt_every, o, o + V, o + 2 * V, J)
+                     : adjoint_impl<float, float>(ctx, (const double*)wd.p, k, ckpt_every, o, o + V, o + 2 * V, J);
     if (rc) return rc;
     const cudaMemcpyKind kind = out_where == RTPN_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     double* dst[3] = {g_sa, g_ss, g_q};

@@ -181,44 +181,68 @@ int stage_variants_of(int N, int precision, int* tiles, int max) {
     return n;
 }
 
-int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long skip_stage,
-                 long long wait_limit) {
-    if (ctx->stage_variant < 0) return (int)cudaErrorNotSupported;
-    const stg::Variant& v = stg::kVariants[ctx->stage_variant];
-    stg::Args a;
-    a.tgt = ctx->u;
-    a.fac = (const float*)ctx->fac;
-    // class cls's targets read the coefficients of the other class's sources (table A = cls)
+// The launch fields every mode shares: geometry, the tile walk, the coupling table of a forward
+// pass on class coef_cls (its sources are the other class), the status word and the wait limit.
+static bool base_args(const rtpn_ctx* ctx, const stg::Variant& v, int coef_cls, stg::Args* out) {
+    stg::Args a{};
     const char* m = (const char*)ctx->stage_mem;
-    a.coefcol = (const float*)(cls == 0 ? m : m + ctx->stage_tab_bytes[0]);
+    a.coefcol = (const float*)(coef_cls == 0 ? m : m + ctx->stage_tab_bytes[0]);
     a.colstart = (const int*)(m + ctx->stage_tab_bytes[0] + ctx->stage_tab_bytes[1]);
     a.V = ctx->g.V;
     a.nx = ctx->g.nx;
     a.ny = ctx->g.ny;
     a.nz = ctx->g.nz;
     a.bc = ctx->g.bc;
-    a.fac_ofs = fac_ofs;
     a.inv_h = (float)(1.0 / ctx->g.h);
     a.ntx = (a.nx + v.tx - 1) / v.tx;
     a.nty = (a.ny + v.ty - 1) / v.ty;
     a.ntz = (a.nz + v.tz - 1) / v.tz;
     a.tiles = (long long)a.ntx * a.nty * a.ntz;
-    if (a.tiles * (ctx->N + 2) >= (1ll << 31)) return (int)cudaErrorInvalidValue;
+    if (a.tiles * (ctx->N + 2) >= (1ll << 31)) return false;
     // z chunk of the tile walk: the ~one tile per SM at work at a time then spans about as many
     // tile rows in y as layers in z, across the whole x extent
-    {
-        const double side = std::sqrt((double)(ctx->sms > 0 ? ctx->sms : 1) / a.ntx);
-        int kz = (int)(side + 0.5);
-        a.kz = kz < 1 ? 1 : (kz > a.ntz ? a.ntz : kz);
-    }
-    a.maps = (const CUtensorMap*)ctx->stage_maps_dev;
-    a.tmap = a.maps;  // target boxes: the tile map over the same state
-    a.src_c0 = cls == 1 ? 0 : ctx->md.ne;  // the source class is the other one
+    const double side = std::sqrt((double)(ctx->sms > 0 ? ctx->sms : 1) / a.ntx);
+    const int kz = (int)(side + 0.5);
+    a.kz = kz < 1 ? 1 : (kz > a.ntz ? a.ntz : kz);
     a.nc = ctx->md.nc;
     a.status = ctx->status;
+    a.wait_limit = (unsigned)STAGE_WAIT_LIMIT;
+    a.skip_stage = -1;
+    *out = a;
+    return true;
+}
+
+// a forward pass on class cls: sources through src_maps, old targets through the plane maps
+// tgt_maps, new targets stored into out (all three may be the context's state)
+static int launch_pass(rtpn_ctx* ctx, int cls, int fac_ofs, const CUtensorMap* src_maps,
+                       const CUtensorMap* tgt_maps, void* out, cudaStream_t st, long long skip_stage,
+                       long long wait_limit) {
+    if (ctx->stage_variant < 0) return (int)cudaErrorNotSupported;
+    const stg::Variant& v = stg::kVariants[ctx->stage_variant];
+    stg::Args a;
+    if (!base_args(ctx, v, cls, &a)) return (int)cudaErrorInvalidValue;
+    a.tgt = out;
+    a.fac = (const float*)ctx->fac;
+    a.fac_ofs = fac_ofs;
+    a.maps = src_maps;
+    a.tmap = tgt_maps;
+    a.src_c0 = cls == 1 ? 0 : ctx->md.ne;  // the source class is the other one
     a.wait_limit = (unsigned)(wait_limit > 0xffffffffll ? 0xffffffffll : wait_limit);
     a.skip_stage = skip_stage;
     return v.launch(cls, ctx->prec, stg::FORWARD, a, ctx->sms, st);
+}
+
+int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long skip_stage,
+                 long long wait_limit) {
+    const CUtensorMap* maps = (const CUtensorMap*)ctx->stage_maps_dev;  // sources and targets: the state
+    return launch_pass(ctx, cls, fac_ofs, maps, maps, ctx->u, st, skip_stage, wait_limit);
+}
+
+int launch_stage_between(rtpn_ctx* ctx, int cls, int fac_ofs, const void* src_maps, const void* tgt_maps,
+                         void* out, cudaStream_t st) {
+    if (ctx->prec != RTPN_FP32) return (int)cudaErrorNotSupported;
+    return launch_pass(ctx, cls, fac_ofs, (const CUtensorMap*)src_maps, (const CUtensorMap*)tgt_maps, out, st,
+                       -1, STAGE_WAIT_LIMIT);
 }
 
 size_t stage_maps_bytes(const rtpn_ctx* ctx) {
@@ -236,52 +260,8 @@ int stage_maps_for(rtpn_ctx* ctx, const void* state, void* maps_dev) {
     return (int)cudaMemcpy(maps_dev, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
 }
 
-int launch_stage_adjoint_targets(rtpn_ctx* ctx, int cls, int fac_ofs, const void* maps_dev, float* lam,
-                                 float* wout, const float* dfac, const double* qsrc, double* gacc, double* gq,
-                                 cudaStream_t st) {
-    if (ctx->stage_variant < 0 || ctx->prec != RTPN_FP32) return (int)cudaErrorNotSupported;
-    const stg::Variant& v = stg::kVariants[ctx->stage_variant];
-    stg::Args a{};
-    a.tgt = nullptr;  // nothing of the state is written
-    a.lam = lam;
-    a.wout = wout;
-    a.dfac = dfac;
-    a.qsrc = qsrc;
-    a.gacc = gacc;
-    a.gq = gq;
-    a.fac = (const float*)ctx->fac;
-    const char* m = (const char*)ctx->stage_mem;
-    a.coefcol = (const float*)(cls == 0 ? m : m + ctx->stage_tab_bytes[0]);
-    a.colstart = (const int*)(m + ctx->stage_tab_bytes[0] + ctx->stage_tab_bytes[1]);
-    a.V = ctx->g.V;
-    a.nx = ctx->g.nx;
-    a.ny = ctx->g.ny;
-    a.nz = ctx->g.nz;
-    a.bc = ctx->g.bc;
-    a.fac_ofs = fac_ofs;
-    a.inv_h = (float)(1.0 / ctx->g.h);
-    a.ntx = (a.nx + v.tx - 1) / v.tx;
-    a.nty = (a.ny + v.ty - 1) / v.ty;
-    a.ntz = (a.nz + v.tz - 1) / v.tz;
-    a.tiles = (long long)a.ntx * a.nty * a.ntz;
-    if (a.tiles * (ctx->N + 2) >= (1ll << 31)) return (int)cudaErrorInvalidValue;
-    {
-        const double side = std::sqrt((double)(ctx->sms > 0 ? ctx->sms : 1) / a.ntx);
-        int kz = (int)(side + 0.5);
-        a.kz = kz < 1 ? 1 : (kz > a.ntz ? a.ntz : kz);
-    }
-    a.maps = (const CUtensorMap*)maps_dev;
-    a.tmap = a.maps;  // the old target values come from the same pre-substep state
-    a.src_c0 = cls == 1 ? 0 : ctx->md.ne;
-    a.nc = ctx->md.nc;
-    a.status = ctx->status;
-    a.wait_limit = (unsigned)STAGE_WAIT_LIMIT;
-    a.skip_stage = -1;
-    return v.launch(cls, RTPN_FP32, stg::ADJ_TARGETS, a, ctx->sms, st);
-}
-
 int launch_stage_adjoint_sources(rtpn_ctx* ctx, int tgt_cls, float* lam, const float* w, int w_planes,
-                                 cudaStream_t st) {
+                                 int fac_ofs, cudaStream_t st) {
     if (ctx->stage_variant < 0 || ctx->prec != RTPN_FP32) return (int)cudaErrorNotSupported;
     const stg::Variant& v = stg::kVariants[ctx->stage_variant];
     // tensor maps over w (every source box kind) and over lam (target planes), rebuilt when the
@@ -298,37 +278,16 @@ int launch_stage_adjoint_sources(rtpn_ctx* ctx, int tgt_cls, float* lam, const f
         ctx->stage_adj_lam = lam;
         ctx->stage_adj_w = w;
     }
-    stg::Args a;
-    a.tgt = lam;
-    a.fac = nullptr;
-    const char* m = (const char*)ctx->stage_mem;
     // the coupling table of a forward pass on the target class: its sources are the other class
-    a.coefcol = (const float*)(tgt_cls == 0 ? m : m + ctx->stage_tab_bytes[0]);
-    a.colstart = (const int*)(m + ctx->stage_tab_bytes[0] + ctx->stage_tab_bytes[1]);
-    a.V = ctx->g.V;
-    a.nx = ctx->g.nx;
-    a.ny = ctx->g.ny;
-    a.nz = ctx->g.nz;
-    a.bc = ctx->g.bc;
-    a.fac_ofs = 0;
-    a.inv_h = (float)(1.0 / ctx->g.h);
-    a.ntx = (a.nx + v.tx - 1) / v.tx;
-    a.nty = (a.ny + v.ty - 1) / v.ty;
-    a.ntz = (a.nz + v.tz - 1) / v.tz;
-    a.tiles = (long long)a.ntx * a.nty * a.ntz;
-    if (a.tiles * (ctx->N + 2) >= (1ll << 31)) return (int)cudaErrorInvalidValue;
-    {
-        const double side = std::sqrt((double)(ctx->sms > 0 ? ctx->sms : 1) / a.ntx);
-        int kz = (int)(side + 0.5);
-        a.kz = kz < 1 ? 1 : (kz > a.ntz ? a.ntz : kz);
-    }
+    stg::Args a;
+    if (!base_args(ctx, v, tgt_cls, &a)) return (int)cudaErrorInvalidValue;
+    a.tgt = lam;
+    a.fac = fac_ofs >= 0 ? (const float*)ctx->fac : nullptr;  // lam_B <- alpha_B lam_B folded in
+    a.fac_ofs = fac_ofs >= 0 ? fac_ofs : 0;
     a.maps = dev;
     a.tmap = dev + stg::MAP_KINDS * nmap;
     a.src_c0 = 0;  // w holds only the source class, in its local order
     a.nc = w_planes;
-    a.status = ctx->status;
-    a.wait_limit = (unsigned)STAGE_WAIT_LIMIT;
-    a.skip_stage = -1;
     return v.launch(tgt_cls, RTPN_FP32, stg::ADJ_SOURCES, a, ctx->sms, st);
 }
 

@@ -123,19 +123,20 @@ int stage_variants_of(int N, int precision, int* tiles, int max);
 int launch_stage(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st, long long skip_stage,
                  long long wait_limit);
 // The transposed coupling of a substep for the adjoint's multipliers on the staged kernel:
-// lam_B += (1/h) K w_A (class B = tgt_cls; w: the w_planes planes of the other class, local order).
-// FP32 contexts with the staged kernel prepared; returns cudaError_t.
+// lam_B <- alpha_B lam_B + (1/h) K w_A (class B = tgt_cls; w: the w_planes planes of the other class,
+// local order; alpha_B the factors at offset fac_ofs (FAC_FULL / FAC_HALF; u_0: its own), or 1 for
+// fac_ofs < 0).  FP32 contexts with the staged kernel prepared; returns cudaError_t.
 int launch_stage_adjoint_sources(rtpn_ctx* ctx, int tgt_cls, float* lam, const float* w, int w_planes,
-                                 cudaStream_t st);
-// The tensor maps of the staged kernel over another FP32 state (an adjoint segment's pre-substep
-// state) into maps_dev (device, stage_maps_bytes(ctx) bytes, 128-byte aligned); returns cudaError_t.
+                                 int fac_ofs, cudaStream_t st);
+// The tensor maps of the staged kernel over another FP32 state (an adjoint segment's state) into
+// maps_dev (device, stage_maps_bytes(ctx) bytes, 128-byte aligned); returns cudaError_t.
 size_t stage_maps_bytes(const rtpn_ctx* ctx);
 int stage_maps_for(rtpn_ctx* ctx, const void* state, void* maps_dev);
-// The pull-back of the multipliers through a substep on class cls from its pre-substep state (maps
-// from stage_maps_for): media gradients into gacc / gq, w of class cls, lam of class cls scaled.
-int launch_stage_adjoint_targets(rtpn_ctx* ctx, int cls, int fac_ofs, const void* maps_dev, float* lam,
-                                 float* wout, const float* dfac, const double* qsrc, double* gacc, double* gq,
-                                 cudaStream_t st);
+// A forward pass on class cls between FP32 states: sources through src_maps, the old targets
+// through the plane maps that start tgt_maps (both from stage_maps_for), the new targets into out
+// (full state layout; only class cls is written).  Returns cudaError_t.
+int launch_stage_between(rtpn_ctx* ctx, int cls, int fac_ofs, const void* src_maps, const void* tgt_maps,
+                         void* out, cudaStream_t st);
 constexpr long long STAGE_WAIT_LIMIT = 1ll << 20;  // mbarrier polls (each <= 2 us) before a wait gives up
 
 }  // namespace rtpn

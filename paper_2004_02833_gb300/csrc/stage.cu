@@ -79,15 +79,11 @@ void geom_of(int* out) {
 
 }  // namespace
 
-// mode FORWARD: FP32 or BF16 storage; modes ADJ_SOURCES, ADJ_TARGETS: FP32 (the adjoint)
+// mode FORWARD: FP32 or BF16 storage; mode ADJ_SOURCES: FP32 (the adjoint)
 int RTPN_SVARIANT(stage_launch)(int cls, int precision, int mode, const Args& a, int sms, cudaStream_t st) {
     if (mode == ADJ_SOURCES) {
         if (precision != RTPN_FP32) return (int)cudaErrorNotSupported;
         return cls == 0 ? launch_one<0, float, ADJ_SOURCES>(a, sms, st) : launch_one<1, float, ADJ_SOURCES>(a, sms, st);
-    }
-    if (mode == ADJ_TARGETS) {
-        if (precision != RTPN_FP32) return (int)cudaErrorNotSupported;
-        return cls == 0 ? launch_one<0, float, ADJ_TARGETS>(a, sms, st) : launch_one<1, float, ADJ_TARGETS>(a, sms, st);
     }
     if (precision == RTPN_BF16)
         return cls == 0 ? launch_one<0, __nv_bfloat16, FORWARD>(a, sms, st)

@@ -84,13 +84,11 @@ constexpr int CPAD = 12;
 
 // What a pass computes.  FORWARD: targets u_A' = alpha u_A - beta acc (Eq. 5; the u_0 factors for
 // l = 0).  ADJ_SOURCES: the transpose of a substep's coupling for the dual multipliers,
-// lam_B' = lam_B + acc / h with the sources the weights w_A = beta_A lam_A of the substep on class A
-// (same stencil rule and coefficient table as a forward pass on class B: see csrc/adjoint.cu).
-// ADJ_TARGETS: the pull-back through a substep on class A of the adjoint's multipliers: from the
-// pre-substep state, the forward residual r_A = -acc / h (+ q for u_0), the media gradients
-// gacc[slot] += lam_A (dalpha u_A + dbeta r_A) (and gq += beta_0 lam_0), w_A = beta_A lam_A and
-// lam_A <- alpha_A lam_A.
-constexpr int FORWARD = 0, ADJ_SOURCES = 1, ADJ_TARGETS = 2;
+// lam_B' = alpha_B lam_B + acc / h with the sources the weights w_A = beta_A lam_A of the substep on
+// class A (same stencil rule and coefficient table as a forward pass on class B: see
+// csrc/adjoint.cu); alpha_B, when factors are given, is the factor of the later substep on class B
+// whose pull-back lam_B <- alpha_B lam_B is folded in here.
+constexpr int FORWARD = 0, ADJ_SOURCES = 1;
 
 // Tensor maps of one array: kind k in {MAP_PLANE, MAP_YROW, MAP_XGRP} for every box length
 // E = EQ, 2 EQ, ..., NL (index k * nmaps + E / EQ - 1).
@@ -100,14 +98,7 @@ constexpr int MAP_XGRP = 2;   // [E][TZ][RY][XW]: the x halo group
 constexpr int MAP_KINDS = 3;
 
 struct Args {
-    void* tgt;              // target array (u for a forward pass, lam for ADJ_SOURCES)
-    // ADJ_TARGETS only
-    float* lam;             // multipliers [nc][V] (internal order), read and scaled in place
-    float* wout;            // w of the target class [local index][V]
-    const float* dfac;      // dalpha/dc, dbeta/dc planes (same slot layout as the factors; u_0: 32, 33)
-    const double* qsrc;     // q per cell (the u_0 source)
-    double* gacc;           // [9][V] media-gradient accumulators (slot codes 0..7, u_0)
-    double* gq;             // [V] source gradient
+    void* tgt;              // target array written (u for a forward pass, lam for ADJ_SOURCES)
     const float* fac;
     const float* coefcol;   // [column 0..N][type][slot q 0..N/2][CPAD] of the source class (0 for l < M)
     const int* colstart;    // [2][N+2]: first local index of column M in class 0 / class 1
@@ -628,7 +619,7 @@ RTPN_HD void sweep_column(const unsigned char* buf, const Operands& op, int T, i
 // Finish target column M of type T (accumulators in prev) from its old values in the stage's
 // target planes (at byte offset tgo for this cell) into global memory: FORWARD by Eq. (5),
 // u' = alpha u - beta acc (the u_0 factors al0, be0, ga0 for slot 0 of column 0, cos type, class 0);
-// ADJ_SOURCES lam' = lam + acc / h.  tp: component q = 0 of the run at this cell, components V
+// ADJ_SOURCES lam' = alpha lam + acc / h (alpha = 1 when no factors are given).  tp: component q = 0 of the run at this cell, components V
 // apart; only an active cell is stored.
 template <int N, int A, typename S, int TX, int TY, int TZ, int NB, int EQ, int MODE>
 RTPN_HD void finish_column(const unsigned char* buf, int tgo, int M, int T, S* tp, long long V, bool active,
@@ -645,7 +636,7 @@ RTPN_HD void finish_column(const unsigned char* buf, int tgo, int M, int T, S* t
             const float old = lds<S>(ob, q * UB);
             float nv;
             if constexpr (MODE == ADJ_SOURCES)
-                nv = fmaf(inv_h, prev[q], old);
+                nv = fmaf(inv_h, prev[q], ((q == 0 && u0) ? al0 : alpha) * old);
             else if (q == 0)
                 nv = u0 ? fmaf(al0, old, fmaf(-be0, prev[q], ga0)) : fmaf(alpha, old, -beta * prev[q]);
             else
@@ -664,7 +655,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     constexpr int B = 1 - A;
     constexpr int NLA = (N - A) / 2 + 1;   // class-A components of a run, at most
     constexpr int CELLS = L::CELLS;
-    constexpr int UB = L::UB, REG = L::REG, ES = L::ES;
+    constexpr int REG = L::REG, ES = L::ES;
     constexpr int NST = N + 2;  // stage i: sources of column i (i <= N), targets of column i - 1
     const int cA0 = A == 0 ? 0 : class_size(N, 0);
     [[maybe_unused]] const int* colA = a.colstart + A * (N + 2);
@@ -714,13 +705,6 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
     Operands op{};                                     // operand offsets, fixed per tile
     float alE = 0.f, beE = 0.f, alO = 0.f, beO = 0.f;  // Eq. (5) factors of columns M even / odd
     float al0 = 0.f, be0 = 0.f, ga0 = 0.f;             // u_0 (class 0, type 0 only)
-    // ADJ_TARGETS: factor derivatives, the u_0 source, the multipliers of the target column being
-    // finished (prefetched at the top of the stage) and this tile's media-gradient sums
-    float daE = 0.f, dbE = 0.f, daO = 0.f, dbO = 0.f, da0 = 0.f, db0 = 0.f, q0s = 0.f;
-    float lpre[MODE == ADJ_TARGETS ? NLA : 1];
-#pragma unroll
-    for (int q = 0; q < (MODE == ADJ_TARGETS ? NLA : 1); ++q) lpre[q] = 0.f;
-    float gE = 0.f, gO = 0.f, g0 = 0.f, gqa = 0.f;
 
     // first local index of target column M in class A, advanced column by column (offA = colstart
     // of the column finished next)
@@ -741,7 +725,7 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
             op = operand_offsets<N, A, S, TX, TY, TZ, NB, EQ>(g, T, lx, ly, lz);
 #pragma unroll
             for (int q = 0; q < NLA; ++q) prev[q] = cur[q] = next[q] = 0.f;
-            if (MODE != ADJ_SOURCES && active) {  // the transposed coupling uses no factors
+            if (active && (MODE == FORWARD || a.fac)) {  // ADJ_SOURCES: the alphas only, if asked
                 // sub-grid slot of (l, M, T) in class A: x by (M, T), y by T, z by (A + M)
 #pragma unroll
                 for (int par = 0; par < 2; ++par) {
@@ -749,9 +733,8 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                     const int gz = ((A + par) & 1) == 0 ? 0 : 1;
                     const int gc = gx + 2 * T + 4 * gz;
                     const float al = __ldg(a.fac + (long long)(a.fac_ofs + 2 * gc) * V + cell);
-                    // the forward folds 1/h into beta; the adjoint keeps beta and da, db per slot
-                    const float be = __ldg(a.fac + (long long)(a.fac_ofs + 2 * gc + 1) * V + cell) *
-                                     (MODE == ADJ_TARGETS ? 1.f : a.inv_h);
+                    // the pass folds 1/h into beta
+                    const float be = __ldg(a.fac + (long long)(a.fac_ofs + 2 * gc + 1) * V + cell) * a.inv_h;
                     if (par == 0) {
                         alE = al;
                         beE = be;
@@ -759,44 +742,20 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
                         alO = al;
                         beO = be;
                     }
-                    if constexpr (MODE == ADJ_TARGETS) {
-                        const float da = __ldg(a.dfac + (long long)(a.fac_ofs + 2 * gc) * V + cell);
-                        const float db = __ldg(a.dfac + (long long)(a.fac_ofs + 2 * gc + 1) * V + cell);
-                        if (par == 0) {
-                            daE = da;
-                            dbE = db;
-                        } else {
-                            daO = da;
-                            dbO = db;
-                        }
-                    }
                 }
                 if (A == 0 && T == 0) {
                     al0 = __ldg(a.fac + (long long)FAC_U0 * V + cell);
-                    be0 = __ldg(a.fac + (long long)(FAC_U0 + 1) * V + cell) * (MODE == ADJ_TARGETS ? 1.f : a.inv_h);
+                    be0 = __ldg(a.fac + (long long)(FAC_U0 + 1) * V + cell) * a.inv_h;
                     ga0 = __ldg(a.fac + (long long)(FAC_U0 + 2) * V + cell);
-                    if constexpr (MODE == ADJ_TARGETS) {
-                        da0 = __ldg(a.dfac + 32ll * V + cell);
-                        db0 = __ldg(a.dfac + 33ll * V + cell);
-                        q0s = (float)a.qsrc[cell];
-                    }
                 }
+            } else if (MODE == ADJ_SOURCES) {
+                alE = alO = al0 = 1.f;
             }
         }
         // target column i - 1 of type T is finished in this stage (the same for the whole warp); the
         // sweep and the finish run on every thread of the tile (a thread past the grid's edge works
         // on zero-filled or in-tile shared memory), only global memory accesses need an active cell
         const bool finw = i >= 1 && (T == 0 || i - 1 >= 1);
-        const bool fin = active && finw;
-        if constexpr (MODE == ADJ_TARGETS) {
-            if (fin) {  // the multipliers of column i - 1, for the finish below
-                const int M = i - 1, q0 = first_l(M, A) / 2;
-                const float* lp = a.lam + (long long)(cA0 + offA + T * column_len(N, M, A) - q0) * V + cell;
-#pragma unroll
-                for (int q = 0; q < NLA; ++q)
-                    if (q >= q0) lpre[q] = __ldg(lp + (long long)q * V);
-            }
-        }
 
         if (!__all_sync(0xffffffffu, wait_phase(full0 + 8 * b, ph, a.wait_limit))) {
             if (lane == 0) atomicOr(a.status, STATUS_TIMEOUT);
@@ -810,45 +769,9 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
             const float alpha = (M & 1) ? alO : alE, beta = (M & 1) ? beO : beE;
             const int q0 = first_l(M, A) / 2;
             (void)RTPN_SCHECK(offA == colA[M]);
-            if constexpr (MODE != ADJ_TARGETS) {
-                S* tp = reinterpret_cast<S*>(a.tgt) + (long long)(cA0 + offA + T * column_len(N, M, A) - q0) * V + cell;
-                finish_column<N, A, S, TX, TY, TZ, NB, EQ, MODE>(buf, tgo, M, T, tp, V, active, alpha, beta, al0, be0,
-                                                                 ga0, a.inv_h, prev);
-            } else {
-                // ---- the pull-back through the substep on class A (see ADJ_TARGETS above)
-                const bool u0 = A == 0 && M == 0 && T == 0;
-                const unsigned char* ob = buf + tgo - q0 * UB;
-                auto tslot = [&](auto qi) {
-                    constexpr int q = decltype(qi)::value;
-                    if constexpr (q < NLA) {
-                        const float old = lds<S>(ob, q * UB);
-                        const float la = lpre[q];
-                        const float r = -a.inv_h * prev[q];  // the forward residual (without q)
-                        const long long loc = (long long)(offA + T * column_len(N, M, A) - q0 + q) * V + cell;
-                        float al, be;
-                        if (q == 0 && u0) {
-                            g0 = fmaf(la, fmaf(da0, old, db0 * (r + q0s)), g0);
-                            gqa = fmaf(be0, la, gqa);
-                            al = al0;
-                            be = be0;
-                        } else {
-                            const float da = (M & 1) ? daO : daE, db = (M & 1) ? dbO : dbE;
-                            const float gv = la * fmaf(da, old, db * r);
-                            if (M & 1)
-                                gO += gv;
-                            else
-                                gE += gv;
-                            al = alpha;
-                            be = beta;
-                        }
-                        if (active) {
-                            a.wout[loc] = be * la;
-                            a.lam[(long long)cA0 * V + loc] = al * la;
-                        }
-                    }
-                };
-                switch (q0) { RTPN_SLOT_CASES(tslot) }
-            }
+            S* tp = reinterpret_cast<S*>(a.tgt) + (long long)(cA0 + offA + T * column_len(N, M, A) - q0) * V + cell;
+            finish_column<N, A, S, TX, TY, TZ, NB, EQ, MODE>(buf, tgo, M, T, tp, V, active, alpha, beta, al0, be0,
+                                                             ga0, a.inv_h, prev);
         }
         // the stage buffer is free once every lane of the warp is past its reads
         __syncwarp();
@@ -861,25 +784,6 @@ __device__ __forceinline__ void stage_kernel_body(const Args& a, unsigned char* 
 #pragma unroll
         for (int q = 0; q < NLA; ++q) prev[q] = 0.f;
         if (i >= 1) offA += ntypes(i - 1) * column_len(N, i - 1, A);
-        if constexpr (MODE == ADJ_TARGETS) {
-            if (i == NST - 1) {
-                // this tile's media-gradient sums: each (cell, slot code) belongs to one thread; a
-                // thread past the grid's edge has summed values of no cell and only clears them
-                if (active) {
-#pragma unroll
-                    for (int par = 0; par < 2; ++par) {
-                        const int gx = ((par == 0) == (T == 0)) ? 0 : 1;
-                        const int gz = ((A + par) & 1) == 0 ? 0 : 1;
-                        a.gacc[(long long)(gx + 2 * T + 4 * gz) * V + cell] += (double)(par == 0 ? gE : gO);
-                    }
-                    if (A == 0 && T == 0) {
-                        a.gacc[8ll * V + cell] += (double)g0;
-                        a.gq[cell] += (double)gqa;
-                    }
-                }
-                gE = gO = g0 = gqa = 0.f;
-            }
-        }
         if (i == NST - 1) offA = 0;  // tile done
         ++s;
         i = (i == NST - 1) ? 0 : i + 1;

@@ -78,6 +78,50 @@ def test_adjoint_staged_kernel_many_tiles_vs_oracle(cuda_device, coupling_cache,
     assert rel(gsa, gsa_ref) <= 1e-4 and rel(gss, gss_ref) <= 1e-4 and rel(gq, gq_ref) <= 1e-4
 
 
+@pytest.mark.parametrize("k,ckpt", [(7, 3), (4, 4), (2, 5), (5, 1)])
+def test_adjoint_staged_segments_vs_oracle(cuda_device, coupling_cache, k, ckpt):
+    # the staged FP32 adjoint runs each checkpoint segment in the merged form of the step, written
+    # out of place: segments of uneven length (7 = 3 + 3 + 1), one segment, a segment shorter than
+    # the checkpoint interval and one step per segment, against the literal schedule of the oracle;
+    # the final state (end of the last segment copied back) too
+    N, shape = 7, (6, 5, 32)
+    inst, u0 = synth.random_instance(N, shape, seed=47, bc="vacuum")
+    w = np.random.default_rng(48).uniform(0.0, 1.0, shape)
+    mats, slots = coupling_cache(N)
+    P = st.Problem(N, inst.sigma_a, inst.sigma_s, inst.q, inst.h, inst.dt, "vacuum", mats=mats, slots=slots)
+    J_ref, gsa_ref, gss_ref, gq_ref = P.gradient(u0, k, w)
+    with rtpn.Context(N, shape, inst.h, "vacuum", "fp32", inst.dt) as ctx:
+        ctx.set_kernel("stage")
+        assert ctx.info().kernel == 3
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        J, (gsa, gss, gq) = ctx.adjoint(w, k, ckpt_every=ckpt)
+        final = ctx.get_moments()
+    assert np.abs(inst.q).max() > 0
+    assert abs(J - J_ref) <= 1e-4 * abs(J_ref)
+    assert rel(gsa, gsa_ref) <= 1e-4 and rel(gss, gss_ref) <= 1e-4 and rel(gq, gq_ref) <= 1e-4
+    assert rel(final, P.run(u0, k)) <= 1e-5
+
+
+@pytest.mark.parametrize("kernel", ["stage", "generic"])
+def test_adjoint_zero_steps(cuda_device, kernel):
+    # k = 0: J is the detector on the current state, every gradient is zero, the state is unchanged
+    N, shape = 7, (4, 4, 32)
+    inst, u0 = synth.random_instance(N, shape, seed=49, bc="periodic")
+    w = np.random.default_rng(50).uniform(0.0, 1.0, shape)
+    with rtpn.Context(N, shape, inst.h, "periodic", "fp32", inst.dt) as ctx:
+        ctx.set_kernel(kernel)
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+        ctx.set_moments(u0)
+        before = ctx.get_moments()
+        J, grads = ctx.adjoint(w, 0, ckpt_every=3)
+        after = ctx.get_moments()
+    J_ref = float((w * before[0].astype(np.float64)).sum())
+    assert abs(J - J_ref) <= 1e-12 * abs(J_ref)
+    assert all(not np.any(g) for g in grads)
+    assert np.array_equal(before, after)
+
+
 def test_adjoint_p3_32_checkerboard_fp64(cuda_device, coupling_cache):
     # P3 on 32^3 in FP64: the lattice scaled to 32^3, vacuum, zero start, detector box scaled
     inst = synth.checkerboard(3, 32)
