@@ -1,10 +1,13 @@
 // Batched form: many independent P_N instances of uneven order and size advanced together.
 //
-// Each pass of the merged Strang schedule (Eq. 6) is ONE persistent launch over the tiles of every
-// instance: CTAs take tiles from a global work counter (heaviest orders first) and run the same
-// compile-time register-window cell body as the single-instance kernel, dispatched on the tile's
-// order N.  Instances are independent, so a pass has no cross-instance dependence; consecutive
-// passes are ordered by the stream.  Whole k-step sequences are replayed from captured CUDA graphs.
+// Each pass of the merged Strang schedule (Eq. 6) is one persistent launch per order present in the
+// batch (heaviest order first), each over the tiles of every instance of that order: CTAs take
+// tiles from the order's work counter (largest instances first) and run the same compile-time
+// register-window cell body as the single-instance kernel.  One launch per order rather than one
+// for all orders: a kernel that dispatches on N at run time is compiled for the registers of its
+// largest order, which caps the occupancy of every smaller order's tiles.  Instances are
+// independent, so a pass has no cross-instance dependence; consecutive passes are ordered by the
+// stream.  Whole k-step sequences are replayed from captured CUDA graphs.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -38,22 +41,18 @@ struct Inst {
     int ntx, nty, ntz;
 };
 
-template <int A, typename S>
-__device__ __forceinline__ void run_cell(int N, const Args& a, int x, int y, int z) {
-    switch (N) {
-#define RTPN_CASE(n)                                                                        \
-    case n:                                                                                 \
-        win::substep_cell<n, A, S>(a, A == 0 ? c_coef_##n##_0 : c_coef_##n##_1, x, y, z); \
-        break;
-        RTPN_BATCH_ORDERS(RTPN_CASE)
+template <int N, int A>
+__device__ __forceinline__ const float* coef_of() {
+#define RTPN_CASE(n) \
+    if constexpr (N == n) return A == 0 ? c_coef_##n##_0 : c_coef_##n##_1;
+    RTPN_BATCH_ORDERS(RTPN_CASE)
 #undef RTPN_CASE
-        default:
-            break;
-    }
+    return nullptr;
 }
 
-// Persistent: each CTA repeatedly takes the next tile index from *counter until all are done.
-template <int A, typename S>
+// Persistent, for the instances of one order N: each CTA repeatedly takes the next tile index from
+// *counter until all of the group's tiles are done.
+template <int N, int A, typename S>
 __global__ void __launch_bounds__(256) k_batch(const Inst* __restrict__ inst, int count,
                                                long long items, int tx, int ty, int tz,
                                                int fac_ofs, unsigned long long* counter) {
@@ -88,7 +87,7 @@ __global__ void __launch_bounds__(256) k_batch(const Inst* __restrict__ inst, in
         a.ntz = I.ntz;
         int x, y, z;
         if (win::cell_of(a, (int)(it - I.block0), threadIdx.x, &x, &y, &z))
-            run_cell<A, S>(I.N, a, x, y, z);
+            win::substep_cell<N, A, S>(a, coef_of<N, A>(), x, y, z);
     }
 }
 
@@ -135,15 +134,21 @@ int upload_constants(const Model& md) {
 
 using namespace rtpn;
 
+// the instances of one order: descriptors [first, first + count) of the device array, tiles
+// numbered from 0 within the group, one persistent launch of `grid` CTAs per pass
+struct BatchGroup {
+    int N = 0, first = 0, count = 0, grid = 0;
+    long long items = 0;
+};
+
 struct rtpn_batch {
     std::vector<rtpn_ctx*> ctx;         // one context per instance (memory, media, moments)
-    std::vector<int> order;             // instances sorted heaviest first
+    std::vector<int> order;             // instances sorted heaviest first (order, then cells)
+    std::vector<BatchGroup> groups;     // one per order present, heaviest order first
     bat::Inst* d_inst = nullptr;        // device descriptors
-    unsigned long long* counter = nullptr;
-    long long items = 0;
+    unsigned long long* counter = nullptr;  // one work counter per group
     int prec = RTPN_FP32;
     int tx = 32, ty = 4, tz = 2;
-    int grid = 0;                       // persistent CTAs
     cudaStream_t stream = nullptr, own = nullptr;
     std::map<int, cudaGraphExec_t> graphs;
     bool media_set_all = false;
@@ -162,12 +167,33 @@ void drop_graphs(rtpn_batch* b) {
     b->graphs.clear();
 }
 
-// (re)build the device descriptors for the current tile
+// the kernel of order N, class A, storage S (for the occupancy query)
+template <int A, typename S>
+const void* kernel_of(int N) {
+    switch (N) {
+#define RTPN_KER(n) \
+    case n:         \
+        return (const void*)bat::k_batch<n, A, S>;
+        RTPN_BATCH_ORDERS(RTPN_KER)
+#undef RTPN_KER
+        default:
+            return nullptr;
+    }
+}
+
+// (re)build the device descriptors and the order groups for the current tile
 int build_items(rtpn_batch* b) {
     std::vector<bat::Inst> h;
-    long long next = 0;
+    b->groups.clear();
     for (int idx : b->order) {
         rtpn_ctx* c = b->ctx[idx];
+        if (b->groups.empty() || b->groups.back().N != c->N) {
+            BatchGroup gr;
+            gr.N = c->N;
+            gr.first = (int)h.size();
+            b->groups.push_back(gr);
+        }
+        BatchGroup& gr = b->groups.back();
         bat::Inst I{};
         I.u = c->u;
         I.fac = (const float*)c->fac;
@@ -181,43 +207,59 @@ int build_items(rtpn_batch* b) {
         I.ntx = (I.nx + b->tx - 1) / b->tx;
         I.nty = (I.ny + b->ty - 1) / b->ty;
         I.ntz = (I.nz + b->tz - 1) / b->tz;
-        I.block0 = next;
-        next += (long long)I.ntx * I.nty * I.ntz;
+        I.block0 = gr.items;
+        gr.items += (long long)I.ntx * I.nty * I.ntz;
+        ++gr.count;
         h.push_back(I);
     }
-    b->items = next;
-    cudaError_t e = cudaMemcpy(b->d_inst, h.data(), h.size() * sizeof(bat::Inst),
-                               cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(b->d_inst, h.data(), h.size() * sizeof(bat::Inst), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bfail(b, RTPN_ECUDA, cudaGetErrorString(e));
-    int per_sm = 0, sms = 0, dev = 0;
+    int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int threads = b->tx * b->ty * b->tz;
-    if (b->prec == RTPN_BF16)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bat::k_batch<0, __nv_bfloat16>,
-                                                          threads, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bat::k_batch<0, float>, threads, 0);
-    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-    b->grid = std::max(1, sms * per_sm);
+    for (auto& gr : b->groups) {
+        // the two classes' kernels differ little in registers: size the grid by the even one's
+        const void* k = b->prec == RTPN_BF16 ? kernel_of<0, __nv_bfloat16>(gr.N) : kernel_of<0, float>(gr.N);
+        int per_sm = 0;
+        e = k ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) : cudaErrorInvalidValue;
+        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+        gr.grid = (int)std::max(1ll, std::min((long long)sms * per_sm, gr.items));
+    }
     drop_graphs(b);
     return RTPN_OK;
 }
 
-int batch_pass(rtpn_batch* b, int cls, int fac_ofs, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return bfail(b, RTPN_ECUDA, cudaGetErrorString(e));
+template <int A, typename S>
+void launch_group(const BatchGroup& gr, rtpn_batch* b, int fac_ofs, unsigned long long* counter, cudaStream_t st) {
     const int threads = b->tx * b->ty * b->tz;
-    const int count = (int)b->order.size();
-#define RTPN_LAUNCH(A, S)                                                                      \
-    bat::k_batch<A, S><<<b->grid, threads, 0, st>>>(b->d_inst, count, b->items, b->tx, b->ty, \
-                                                    b->tz, fac_ofs, b->counter)
-    if (b->prec == RTPN_BF16) {
-        if (cls == 0) RTPN_LAUNCH(0, __nv_bfloat16); else RTPN_LAUNCH(1, __nv_bfloat16);
-    } else {
-        if (cls == 0) RTPN_LAUNCH(0, float); else RTPN_LAUNCH(1, float);
-    }
+    switch (gr.N) {
+#define RTPN_LAUNCH(n)                                                                              \
+    case n:                                                                                         \
+        bat::k_batch<n, A, S><<<gr.grid, threads, 0, st>>>(b->d_inst + gr.first, gr.count, gr.items, \
+                                                           b->tx, b->ty, b->tz, fac_ofs, counter);  \
+        break;
+        RTPN_BATCH_ORDERS(RTPN_LAUNCH)
 #undef RTPN_LAUNCH
+        default:
+            break;
+    }
+}
+
+int batch_pass(rtpn_batch* b, int cls, int fac_ofs, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b->counter, 0, b->groups.size() * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return bfail(b, RTPN_ECUDA, cudaGetErrorString(e));
+    for (size_t k = 0; k < b->groups.size(); ++k) {
+        const BatchGroup& gr = b->groups[k];
+        unsigned long long* ctr = b->counter + k;
+        if (b->prec == RTPN_BF16) {
+            if (cls == 0) launch_group<0, __nv_bfloat16>(gr, b, fac_ofs, ctr, st);
+            else launch_group<1, __nv_bfloat16>(gr, b, fac_ofs, ctr, st);
+        } else {
+            if (cls == 0) launch_group<0, float>(gr, b, fac_ofs, ctr, st);
+            else launch_group<1, float>(gr, b, fac_ofs, ctr, st);
+        }
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(b, RTPN_ECUDA, std::string("batch kernel: ") + cudaGetErrorString(e));
     return RTPN_OK;
@@ -315,7 +357,7 @@ int rtpn_batch_create(rtpn_batch** out, int count, const int* N, const int* nx, 
         return (long long)nx[x] * ny[x] * nz[x] > (long long)nx[y] * ny[y] * nz[y];
     });
     if (cudaMalloc(&b->d_inst, sizeof(bat::Inst) * count) != cudaSuccess ||
-        cudaMalloc(&b->counter, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&b->counter, sizeof(unsigned long long) * count) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->own, cudaStreamDefault) != cudaSuccess) {
         release(b);
         delete b;
