@@ -278,6 +278,17 @@ int rtpn_adjoint(rtpn_ctx* ctx, const void* w, int dtype, int where, int k, int 
                  double* g_sa, double* g_ss, double* g_q, int out_where, double* J);
 
 /*
+ * Frees the work buffers rtpn_adjoint keeps between calls.  With the staged kernel active (FP32)
+ * the checkpoints, segment states, multipliers and tensor maps of a call stay allocated on the
+ * context's device (about (k/ckpt_every + ckpt_every + 4) states), so that the next call with the
+ * same or a smaller k/ckpt_every layout neither allocates nor rebuilds its tensor maps (the
+ * backward of a training loop); rtpn_destroy frees them too.  Not from the paper: workspace
+ * management of this library.  Waits for the context's stream first.  RTPN_ECUDA if the free
+ * fails; a context without kept buffers returns RTPN_OK.
+ */
+int rtpn_adjoint_release(rtpn_ctx* ctx);
+
+/*
  * The detector functional that rtpn_adjoint differentiates, on the current state:
  *     J = sum over cells of w * u_0
  * accumulated in FP64 in a fixed order (1024 block partials, then one block; deterministic).  The

@@ -19,6 +19,7 @@
 // k_adj_sources.  FP32 storage on the staged kernel runs the merged form of the step with
 // out-of-place segment states and a cell-by-cell pull-back (adjoint_staged).  Gradient accumulators
 // are FP64.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -564,26 +565,7 @@ int adjoint_staged(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* 
     const int nring = std::min(k, ckpt) + 1;  // X[1] .. X[m + 1] of the longest segment
     const size_t mapb = stage_maps_bytes(ctx);
     if (V % 4 != 0 || mapb == 0) return afail(ctx, RTPN_EUNSUPPORTED, "adjoint: staged kernel layout");
-    Buf ck, ring, lam, wbuf, dfac, gacc, gqb, part, maps, tabs;
-    if (!ck.alloc(state * std::max(nseg, 1)) || !ring.alloc(state * nring) || !lam.alloc(state) ||
-        !wbuf.alloc((size_t)std::max(ne, no) * V * sizeof(float)) ||
-        !dfac.alloc((size_t)DFAC_PLANES * V * sizeof(float)) || !gacc.alloc((size_t)9 * V * sizeof(double)) ||
-        !gqb.alloc((size_t)V * sizeof(double)) || !part.alloc(1024 * sizeof(double)) ||
-        !maps.alloc((size_t)(nseg + nring) * mapb))
-        return afail(ctx, RTPN_ENOMEM, "adjoint: device memory for checkpoints and segment states");
-    auto X = [&](int sg, int i) -> char* {
-        return i == 0 ? (char*)ck.p + (size_t)sg * state : (char*)ring.p + (size_t)(i - 1) * state;
-    };
-    auto XM = [&](int sg, int i) -> const char* {
-        return (const char*)maps.p + (size_t)(i == 0 ? sg : nseg + i - 1) * mapb;
-    };
-    for (int sg = 0; sg < nseg; ++sg)
-        if (stage_maps_for(ctx, X(sg, 0), (char*)maps.p + (size_t)sg * mapb))
-            return afail(ctx, RTPN_ECUDA, "adjoint: tensor maps");
-    for (int i = 1; i <= nring; ++i)
-        if (stage_maps_for(ctx, X(0, i), (char*)maps.p + (size_t)(nseg + i - 1) * mapb))
-            return afail(ctx, RTPN_ECUDA, "adjoint: tensor maps");
-    // the pull-back's component groups of both classes in one device array
+    // the pull-back's component groups of both classes, for one device array
     PullTable pt[2] = {pull_table(ctx->md, 0), pull_table(ctx->md, 1)};
     std::vector<int> all;
     size_t at[2][2];
@@ -593,10 +575,52 @@ int adjoint_staged(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* 
         at[c][1] = all.size();
         all.insert(all.end(), pt[c].idx.begin(), pt[c].idx.end());
     }
-    if (!tabs.alloc(all.size() * sizeof(int)) ||
-        cudaMemcpy(tabs.p, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
-        return afail(ctx, RTPN_ENOMEM, "adjoint: tables");
-    k_adj_factors<float><<<blocks_for(V), 256, 0, st>>>(ctx->media, ctx->media + V, (float*)dfac.p, g, ctx->dt);
+    // work buffers carved from the context's workspace, which is kept between calls
+    enum { CK, RING, LAM, WB, DFAC, GACC, GQ, PART, MAPS, TABS, NBUF };
+    const size_t need[NBUF] = {state * std::max(nseg, 1), state * nring, state,
+                               (size_t)std::max(ne, no) * V * sizeof(float),
+                               (size_t)DFAC_PLANES * V * sizeof(float), (size_t)9 * V * sizeof(double),
+                               (size_t)V * sizeof(double), 1024 * sizeof(double), (size_t)(nseg + nring) * mapb,
+                               all.size() * sizeof(int)};
+    size_t off[NBUF], total = 0;
+    for (int k = 0; k < NBUF; ++k) {
+        off[k] = total;
+        total += (need[k] + 255) / 256 * 256;
+    }
+    if (ctx->adj_ws_bytes < total) {
+        if (ctx->adj_ws) cudaFree(ctx->adj_ws);
+        ctx->adj_ws = nullptr;
+        ctx->adj_ws_bytes = 0;
+        if (cudaMalloc(&ctx->adj_ws, total) != cudaSuccess) {
+            ctx->adj_ws = nullptr;
+            cudaGetLastError();
+            return afail(ctx, RTPN_ENOMEM, "adjoint: device memory for checkpoints and segment states");
+        }
+        ctx->adj_ws_bytes = total;
+    }
+    char* ws = (char*)ctx->adj_ws;
+    char *ck = ws + off[CK], *ring = ws + off[RING], *lam = ws + off[LAM], *wbuf = ws + off[WB];
+    char *dfac = ws + off[DFAC], *gacc = ws + off[GACC], *gqb = ws + off[GQ], *part = ws + off[PART];
+    char *maps = ws + off[MAPS], *tabs = ws + off[TABS];
+    auto X = [&](int sg, int i) -> char* {
+        return i == 0 ? ck + (size_t)sg * state : ring + (size_t)(i - 1) * state;
+    };
+    auto XM = [&](int sg, int i) -> const char* { return maps + (size_t)(i == 0 ? sg : nseg + i - 1) * mapb; };
+    // tensor maps over every checkpoint and ring state, unless the last call built the same ones
+    const long long key[4] = {nseg, nring, ctx->stage_variant, (long long)(size_t)ws};
+    if (!std::equal(key, key + 4, ctx->adj_maps_key)) {
+        std::fill(ctx->adj_maps_key, ctx->adj_maps_key + 4, -1);
+        for (int sg = 0; sg < nseg; ++sg)
+            if (stage_maps_for(ctx, X(sg, 0), maps + (size_t)sg * mapb))
+                return afail(ctx, RTPN_ECUDA, "adjoint: tensor maps");
+        for (int i = 1; i <= nring; ++i)
+            if (stage_maps_for(ctx, X(0, i), maps + (size_t)(nseg + i - 1) * mapb))
+                return afail(ctx, RTPN_ECUDA, "adjoint: tensor maps");
+        std::copy(key, key + 4, ctx->adj_maps_key);
+    }
+    if (cudaMemcpyAsync(tabs, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return afail(ctx, RTPN_ECUDA, "adjoint: tables");
+    k_adj_factors<float><<<blocks_for(V), 256, 0, st>>>(ctx->media, ctx->media + V, (float*)dfac, g, ctx->dt);
 
     auto seg_steps = [&](int sg) { return std::min(k, (sg + 1) * ckpt) - sg * ckpt; };
     auto pass_cls = [](int j) { return (j & 1) ? 0 : 1; };
@@ -624,17 +648,17 @@ int adjoint_staged(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* 
         cudaMemcpyAsync(dst + even_b, X(sg, m + 1) + even_b, odd_b, cudaMemcpyDeviceToDevice, st);
     }
     // J = sum w u_0 (u_0 is internal component 0)
-    k_dot_u0<float><<<1024, 256, 0, st>>>((const float*)ctx->u, w_dev, V, (double*)part.p);
-    launch_sum<double>((const double*)part.p, 1024, ctx->partial, 1, ctx->partial + SUM_BLOCKS, st);
+    k_dot_u0<float><<<1024, 256, 0, st>>>((const float*)ctx->u, w_dev, V, (double*)part);
+    launch_sum<double>((const double*)part, 1024, ctx->partial, 1, ctx->partial + SUM_BLOCKS, st);
     cudaMemcpyAsync(J, ctx->partial + SUM_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st);
 
     // ---- backward, pass by pass in reverse
-    float* lp = (float*)lam.p;
+    float* lp = (float*)lam;
     cudaMemsetAsync(lp, 0, state, st);
     k_copy_cast<double, float><<<1024, 256, 0, st>>>(w_dev, lp, V);  // lam_0 = w
-    cudaMemsetAsync(gacc.p, 0, (size_t)9 * V * sizeof(double), st);
-    cudaMemsetAsync(gqb.p, 0, (size_t)V * sizeof(double), st);
-    const int* tp = (const int*)tabs.p;
+    cudaMemsetAsync(gacc, 0, (size_t)9 * V * sizeof(double), st);
+    cudaMemsetAsync(gqb, 0, (size_t)V * sizeof(double), st);
+    const int* tp = (const int*)tabs;
     // pend[c]: the factor offset of the last pulled-back pass on class c whose lam_c <- alpha lam_c
     // is still to come (folded into the next transposed coupling onto class c), -1 for none
     int pend[2] = {-1, -1};
@@ -648,18 +672,18 @@ int adjoint_staged(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* 
             const int ng = (int)pt[cls].grp.size() / 4;
             const float* pre = (const float*)X(sg, j / 2) + a0;
             const float* post = (const float*)X(sg, j / 2 + 1) + a0;
-            k_adj_pull<<<blocks_for(V / 4), 256, 0, st>>>(pre, post, lp + a0, (float*)wbuf.p, (const float*)ctx->fac,
-                                                          (const float*)dfac.p, ofs, pend[cls], tp + at[cls][0], ng,
-                                                          tp + at[cls][1], V, (double*)gacc.p, (double*)gqb.p);
+            k_adj_pull<<<blocks_for(V / 4), 256, 0, st>>>(pre, post, lp + a0, (float*)wbuf, (const float*)ctx->fac,
+                                                          (const float*)dfac, ofs, pend[cls], tp + at[cls][0], ng,
+                                                          tp + at[cls][1], V, (double*)gacc, (double*)gqb);
             pend[cls] = ofs;
-            const int rc = launch_stage_adjoint_sources(ctx, 1 - cls, lp, (const float*)wbuf.p, std::max(ne, no),
+            const int rc = launch_stage_adjoint_sources(ctx, 1 - cls, lp, (const float*)wbuf, std::max(ne, no),
                                                         pend[1 - cls], st);
             if (rc) return afail(ctx, RTPN_ECUDA, "adjoint: staged transposed coupling failed");
             pend[1 - cls] = -1;
         }
     }
-    k_adj_media<<<blocks_for(V), 256, 0, st>>>((const double*)gacc.p, g, gsa, gss);
-    cudaMemcpyAsync(gq_out, gqb.p, (size_t)V * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    k_adj_media<<<blocks_for(V), 256, 0, st>>>((const double*)gacc, g, gsa, gss);
+    cudaMemcpyAsync(gq_out, gqb, (size_t)V * sizeof(double), cudaMemcpyDeviceToDevice, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(ctx, RTPN_ECUDA, std::string("adjoint: ") + cudaGetErrorString(e));
     if (int rc = rtpn_synchronize(ctx)) return rc;  // also reports a staged wait that ran out
@@ -706,6 +730,19 @@ extern "C" int rtpn_adjoint(rtpn_ctx* ctx, const void* w, int dtype, int where, 
     for (int i = 0; i < 3; ++i) cudaMemcpyAsync(dst[i], o + (size_t)i * V, V * sizeof(double), kind, ctx->stream);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return afail(ctx, RTPN_ECUDA, cudaGetErrorString(e));
+    return RTPN_OK;
+}
+
+extern "C" int rtpn_adjoint_release(rtpn_ctx* ctx) {
+    if (!ctx) return RTPN_EINVAL;
+    if (ctx->adj_ws) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e == cudaSuccess) e = cudaFree(ctx->adj_ws);
+        ctx->adj_ws = nullptr;
+        ctx->adj_ws_bytes = 0;
+        std::fill(ctx->adj_maps_key, ctx->adj_maps_key + 4, -1);
+        if (e != cudaSuccess) return afail(ctx, RTPN_ECUDA, std::string("adjoint release: ") + cudaGetErrorString(e));
+    }
     return RTPN_OK;
 }
 

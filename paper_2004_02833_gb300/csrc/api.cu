@@ -330,6 +330,10 @@ void release(rtpn_ctx* ctx) {
     if (ctx->stage_mem) cudaFree(ctx->stage_mem);
     if (ctx->stage_maps_dev) cudaFree(ctx->stage_maps_dev);
     ctx->stage_maps_dev = nullptr;
+    if (ctx->adj_ws) cudaFree(ctx->adj_ws);
+    ctx->adj_ws = nullptr;
+    ctx->adj_ws_bytes = 0;
+    for (long long& k : ctx->adj_maps_key) k = -1;
     ctx->status = nullptr;
     ctx->stage_mem = nullptr;
     if (ctx->own) cudaStreamDestroy(ctx->own);

@@ -177,4 +177,9 @@ struct rtpn_ctx {
                                      // u, then the adjoint's (over its w, then over its lam)
     const void* stage_adj_lam = nullptr;  // arrays the adjoint maps were built for
     const void* stage_adj_w = nullptr;
+    // the staged FP32 adjoint's work buffers (checkpoints, segment states, multipliers, tensor maps
+    // over them), kept between calls; rtpn_adjoint_release frees them
+    void* adj_ws = nullptr;
+    size_t adj_ws_bytes = 0;
+    long long adj_maps_key[4] = {-1, -1, -1, -1};  // (segments, ring states, variant, workspace) of the maps
 };

@@ -70,6 +70,7 @@ SIGNATURES = {
     "rtpn_synchronize": (_I, [_P]),
     "rtpn_test_wait_timeout": (_I, [_P, _I, ctypes.c_longlong]),
     "rtpn_adjoint": (_I, [_P, _P, _I, _I, _I, _I, _P, _P, _P, _I, ctypes.POINTER(_D)]),
+    "rtpn_adjoint_release": (_I, [_P]),
     "rtpn_detector": (_I, [_P, _P, _I, _I, _P, _I]),
     "rtpn_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _P, _P, _P, _P, _P, _P, _I]),
     "rtpn_batch_destroy": (_I, [_P]),
@@ -305,6 +306,10 @@ class Context:
         self._chk(lib().rtpn_adjoint(self._p, ptr, code, where, int(k), int(ckpt_every), bufs[0][0],
                                      bufs[1][0], bufs[2][0], ow.pop(), ctypes.byref(J)))
         return J.value, out
+
+    def adjoint_release(self):
+        """Free the work buffers the adjoint keeps on the device between calls."""
+        self._chk(lib().rtpn_adjoint_release(self._p))
 
     def detector(self, w, out=None):
         """J = sum w u_0 on the current state (FP64, fixed order).  With `out` (a one-element float64

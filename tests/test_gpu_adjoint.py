@@ -103,6 +103,33 @@ def test_adjoint_staged_segments_vs_oracle(cuda_device, coupling_cache, k, ckpt)
     assert rel(final, P.run(u0, k)) <= 1e-5
 
 
+def test_adjoint_workspace_kept_between_calls(cuda_device):
+    # the staged adjoint keeps its work buffers and tensor maps: a second call with the same layout,
+    # one with a smaller layout, one after rtpn_adjoint_release and one with a larger layout all give
+    # the first call's result bit for bit (same inputs, same launches)
+    N, shape = 7, (6, 5, 32)
+    inst, u0 = synth.random_instance(N, shape, seed=51, bc="vacuum")
+    w = np.random.default_rng(52).uniform(0.0, 1.0, shape)
+    with rtpn.Context(N, shape, inst.h, "vacuum", "fp32", inst.dt) as ctx:
+        ctx.set_kernel("stage")
+        ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+
+        def run(k, ckpt):
+            ctx.set_moments(u0)
+            J, g = ctx.adjoint(w, k, ckpt_every=ckpt)
+            return J, np.stack(g)
+
+        first = run(6, 3)
+        for k, ckpt, release in ((6, 3, False), (2, 2, False), (6, 3, True), (6, 3, False), (9, 3, False)):
+            if release:
+                ctx.adjoint_release()
+            got = run(k, ckpt)
+            if (k, ckpt) == (6, 3):
+                assert got[0] == first[0] and np.array_equal(got[1], first[1])
+        ctx.adjoint_release()
+        ctx.adjoint_release()  # a context without kept buffers
+
+
 @pytest.mark.parametrize("kernel", ["stage", "generic"])
 def test_adjoint_zero_steps(cuda_device, kernel):
     # k = 0: J is the detector on the current state, every gradient is zero, the state is unchanged
