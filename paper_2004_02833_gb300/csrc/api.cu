@@ -360,19 +360,22 @@ int choose_kernel(rtpn_ctx* ctx) {
             return fail(ctx, RTPN_EUNSUPPORTED, "anisotropic scattering runs on the generic kernel only");
         k = RTPN_KERNEL_GENERIC;
     }
+    // the window kernel takes non-cubic cells up to N = 15 (scaled y and z differences); the fused
+    // kernel takes cubic cells only
+    const bool win_ok = window_supported(ctx->N, ctx->prec) && (cubic || window_takes_non_cubic(ctx->N));
     if (k == RTPN_KERNEL_AUTO) {
-        // the window kernels' coupling constants are shared by every context of the process, so
-        // they take cubic cells only; the staged and generic kernels keep theirs per context
         const bool tile_set = ctx->tx || ctx->ty || ctx->tz;
-        if (kStageInAuto && (ctx->N >= kStageMinN || !cubic) &&
+        if (kStageInAuto && (ctx->N >= kStageMinN || !win_ok) &&
             stage_supported(ctx->N, ctx->prec, ctx->g.nx) &&
             (!tile_set || stage_has_tile(ctx->N, ctx->tx, ctx->ty, ctx->tz, ctx->depth, ctx->prec)))
             k = RTPN_KERNEL_STAGE;
         else
-            k = cubic && window_supported(ctx->N, ctx->prec) ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
+            k = win_ok ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
     }
-    if (!cubic && (k == RTPN_KERNEL_WINDOW || k == RTPN_KERNEL_FUSED))
-        return fail(ctx, RTPN_EUNSUPPORTED, "the window and fused kernels take cubic cells only");
+    if (!cubic && k == RTPN_KERNEL_FUSED)
+        return fail(ctx, RTPN_EUNSUPPORTED, "the fused kernel takes cubic cells only");
+    if (!cubic && k == RTPN_KERNEL_WINDOW && !window_takes_non_cubic(ctx->N))
+        return fail(ctx, RTPN_EUNSUPPORTED, "the window kernel takes non-cubic cells up to N = 15 only");
     if (k == RTPN_KERNEL_STAGE) {
         if (!stage_supported(ctx->N, ctx->prec, ctx->g.nx))
             return fail(ctx, RTPN_EUNSUPPORTED,
@@ -557,8 +560,9 @@ int rtpn_set_spacing(rtpn_ctx* ctx, double hx, double hy, double hz) {
         ctx->g = old;
         return fail(ctx, code, msg);
     };
-    if (!cubic && (ctx->kernel == RTPN_KERNEL_WINDOW || ctx->kernel == RTPN_KERNEL_FUSED))
-        return restore(RTPN_EUNSUPPORTED, "the window and fused kernels take cubic cells only");
+    if (!cubic && (ctx->kernel == RTPN_KERNEL_FUSED ||
+                   (ctx->kernel == RTPN_KERNEL_WINDOW && !window_takes_non_cubic(ctx->N))))
+        return restore(RTPN_EUNSUPPORTED, "the fused kernel, and the window kernel above N = 15, take cubic cells only");
     // the partner tables and the staged kernel's constants carry the spacing: rebuild them
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     if (ctx->table_mem) cudaFree(ctx->table_mem);

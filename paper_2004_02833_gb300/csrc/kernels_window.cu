@@ -45,6 +45,8 @@ bool window_supported(int N, int precision) {
     return precision != RTPN_FP64 && win::find(N) != nullptr;
 }
 
+bool window_takes_non_cubic(int N) { return N <= win::kScaledMaxN; }
+
 int window_prepare(const Model& md, double, int precision) {
     static std::mutex mu;
     static std::set<std::pair<int, int>> done;  // (N, device)
@@ -78,6 +80,8 @@ int launch_window(int N, int precision, const WindowLaunch& w, cudaStream_t st) 
     a.bc = w.g.bc;
     a.fac_ofs = w.fac_ofs;
     a.inv_h = (float)(1.0 / w.g.h);
+    a.sy = (float)(w.g.h / w.g.hy);  // exactly 1 for cubic cells
+    a.sz = (float)(w.g.h / w.g.hz);
     a.tx = w.tx > 0 ? w.tx : 32;
     a.ty = w.ty > 0 ? w.ty : 4;
     a.tz = w.tz > 0 ? w.tz : 2;

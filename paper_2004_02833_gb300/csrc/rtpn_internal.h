@@ -87,6 +87,7 @@ struct WindowLaunch {
 };
 // returns false if (N, precision) is not compiled in
 bool window_supported(int N, int precision);
+bool window_takes_non_cubic(int N);  // the window kernel's scaled form is compiled for this N
 // uploads the coefficient constants of order N (idempotent); returns cudaError_t
 int window_prepare(const Model& md, double h, int precision);
 int launch_window(int N, int precision, const WindowLaunch& w, cudaStream_t st);

@@ -26,11 +26,11 @@ static_assert(kSources * 10 * 4 <= 64 * 1024 - 1024, "coefficient table exceeds 
 // coefficient of source j (class 1 - kA, local index) for relation k: M_d[a][b] * dir
 __constant__ float c_coef[kSources * 10];
 
-template <typename S>
+template <typename S, bool SCALED>
 __global__ void __launch_bounds__(256) k_window(Args a) {
     int x, y, z;
     if (!cell_of(a, blockIdx.x, threadIdx.x, &x, &y, &z)) return;
-    substep_cell<kN, kA, S>(a, c_coef, x, y, z);
+    substep_cell<kN, kA, S, SCALED>(a, c_coef, x, y, z);
 }
 
 }  // namespace
@@ -43,10 +43,20 @@ int RTPN_VARIANT(window_upload)(const float* host, int count) {
 int RTPN_VARIANT(window_launch)(int precision, const Args& a, cudaStream_t st) {
     const int threads = a.tx * a.ty * a.tz;
     const unsigned blocks = (unsigned)a.ntx * a.nty * a.ntz;
+    if (a.sy != 1.f || a.sz != 1.f) {
+        if constexpr (kN <= kScaledMaxN) {
+            if (precision == RTPN_BF16)
+                k_window<__nv_bfloat16, true><<<blocks, threads, 0, st>>>(a);
+            else
+                k_window<float, true><<<blocks, threads, 0, st>>>(a);
+            return (int)cudaGetLastError();
+        }
+        return (int)cudaErrorNotSupported;
+    }
     if (precision == RTPN_BF16)
-        k_window<__nv_bfloat16><<<blocks, threads, 0, st>>>(a);
+        k_window<__nv_bfloat16, false><<<blocks, threads, 0, st>>>(a);
     else
-        k_window<float><<<blocks, threads, 0, st>>>(a);
+        k_window<float, false><<<blocks, threads, 0, st>>>(a);
     return (int)cudaGetLastError();
 }
 

@@ -157,6 +157,7 @@ struct Args {
     float inv_h;        // 1 / h (the constants hold M_d[a][b] * dir without it)
     int tx, ty, tz;     // CTA tile (threads = tx*ty*tz)
     int ntx, nty, ntz;  // tiles per axis
+    float sy = 1.f, sz = 1.f;  // h / h_y, h / h_z: the y and z differences' scale (non-cubic cells)
 };
 
 // coef[j * 10 + k]: source j (local index in class B), relation k: M_d[a][b] * dir, where dir = +1 if
@@ -174,7 +175,12 @@ RTPN_HD bool cell_of(const Args& a, int blk, int tid, int* x, int* y, int* z) {
     return *x < a.nx && *y < a.ny && *z < a.nz;
 }
 
-template <int N, int A, typename S>
+// SCALED: non-cubic cells (Section 2.1 divides each difference by its own axis' cell size); the
+// y and z differences are scaled by h / h_y and h / h_z, and 1/h (of x) is applied per target.
+// Compiled up to order kScaledMaxN: P39 runs non-cubic cells on the staged kernel, and its window
+// body is the slowest to compile.
+constexpr int kScaledMaxN = 15;
+template <int N, int A, typename S, bool SCALED = false>
 RTPN_HD void substep_cell(const Args& a, const float* __restrict__ coef, int x, int y, int z) {
     constexpr int B = 1 - A;
     constexpr int NL = N / 2 + 1;
@@ -279,6 +285,7 @@ RTPN_HD void substep_cell(const Args& a, const float* __restrict__ coef, int x, 
                                 constexpr int side = sl[ax] == 1 ? 1 : 0;
                                 const float nb = ok[ax][side] ? load_nc<S>(p + off[ax][side]) : 0.f;
                                 d[ax] = nb - c;
+                                if constexpr (SCALED && ax > 0) d[ax] *= ax == 1 ? a.sy : a.sz;
                             }
                         });
                         static_for<10>([&](auto ki) {

@@ -3,9 +3,10 @@
 // factor buffers).  The factor planes follow the rule of rtpn_set_media (mean of sigma over the
 // cells adjacent to a sub-grid point; alpha = exp(-c tau), beta = tau E(-c tau)).
 //
-// usage: emulate_window N cls nx ny nz bc h dt half fp32|bf16 in.bin out.bin
+// usage: emulate_window N cls nx ny nz bc h dt half fp32|bf16 in.bin out.bin [hy hz]
 //   in.bin: float64 u [n_c][nz][ny][nx] (interface order), then sigma_a, sigma_s, q [nz][ny][nx]
 //   out.bin: float64 u after the substep of class cls (tau = dt, or dt/2 with half = 1)
+//   hy hz: cell sizes along y and z (non-cubic cells: the body's scaled form), default h
 #include <cstdio>
 #include <cstdlib>
 #include <cmath>
@@ -27,18 +28,27 @@ static void check_ptr(const void* p) {
 
 using namespace rtpn;
 
-template <int N, int A, typename S>
+template <int N, int A, typename S, bool SC>
 void run(const win::Args& a, const float* coef) {
     for (int z = 0; z < a.nz; ++z)
         for (int y = 0; y < a.ny; ++y)
-            for (int x = 0; x < a.nx; ++x) win::substep_cell<N, A, S>(a, coef, x, y, z);
+            for (int x = 0; x < a.nx; ++x) win::substep_cell<N, A, S, SC>(a, coef, x, y, z);
+}
+
+template <typename S, bool SC>
+void dispatch_sc(int N, int A, const win::Args& a, const float* coef) {
+#define CASE(n) if (N == n) { if (A == 0) run<n, 0, S, SC>(a, coef); else run<n, 1, S, SC>(a, coef); return; }
+    CASE(1) CASE(3) CASE(7) CASE(15)
+#undef CASE
+    fprintf(stderr, "N not compiled\n"); std::abort();
 }
 
 template <typename S>
 void dispatch(int N, int A, const win::Args& a, const float* coef) {
-#define CASE(n) if (N == n) { if (A == 0) run<n, 0, S>(a, coef); else run<n, 1, S>(a, coef); return; }
-    CASE(1) CASE(3) CASE(7) CASE(15)
-    fprintf(stderr, "N not compiled\n"); std::abort();
+    if (a.sy != 1.f || a.sz != 1.f)
+        dispatch_sc<S, true>(N, A, a, coef);
+    else
+        dispatch_sc<S, false>(N, A, a, coef);
 }
 
 int main(int argc, char** argv) {
@@ -47,6 +57,7 @@ int main(int argc, char** argv) {
     int bc = atoi(argv[6]); double h = atof(argv[7]), dt = atof(argv[8]); int half = atoi(argv[9]);
     std::string prec = argv[10];
     const char* inf = argv[11]; const char* outf = argv[12];
+    const double hy = argc > 14 ? atof(argv[13]) : h, hz = argc > 14 ? atof(argv[14]) : h;
     Model md = build_model(N);
     long long V = (long long)nx * ny * nz;
     std::vector<double> in((size_t)(md.nc + 3) * V);
@@ -84,6 +95,7 @@ int main(int argc, char** argv) {
     win::Args a{};
     a.fac = fac.data(); a.V = V; a.nx = nx; a.ny = ny; a.nz = nz; a.bc = bc;
     a.fac_ofs = half ? FAC_HALF : FAC_FULL; a.inv_h = (float)(1.0 / h);
+    a.sy = (float)(h / hy); a.sz = (float)(h / hz);
     a.tx = a.ty = a.tz = 1; a.ntx = nx; a.nty = ny; a.ntz = nz;
     g_lo[0] = (const char*)fac.data(); g_hi[0] = (const char*)(fac.data() + fac.size());
     std::vector<double> out((size_t)md.nc * V);

@@ -1,6 +1,7 @@
 """Non-cubic cells (hx, hy, hz): the GPU path against the oracle, whose differences divide by the
-cell size of their own axis (Section 2.1), for the kernels that take them (staged, generic) and the
-adjoint; the window, fused and batched kernels refuse them.  Same bounds as the cubic tests."""
+cell size of their own axis (Section 2.1), for the kernels that take them (staged, generic, the
+window kernel up to N = 15) and the adjoint; the fused and batched kernels and the P39 window
+kernel refuse them.  Same bounds as the cubic tests."""
 import numpy as np
 import pytest
 
@@ -27,8 +28,13 @@ CASES = [
     # N, shape (nz, ny, nx), bc, kernel, precision, expected kernel id
     (3, (5, 6, 7), "vacuum", "generic", "fp64", 1),
     (7, (6, 7, 9), "periodic", "generic", "fp32", 1),
-    (7, (5, 6, 32), "vacuum", "auto", "fp32", 3),       # the staged kernel (compiled for N = 7)
-    (5, (4, 5, 6), "periodic", "auto", "fp32", 1),      # no staged variant: generic
+    (7, (5, 6, 32), "vacuum", "stage", "fp32", 3),      # the staged kernel (compiled for N = 7)
+    (7, (5, 6, 32), "vacuum", "auto", "fp32", 2),       # below N = 15 the window kernel
+    (5, (4, 5, 6), "periodic", "auto", "fp32", 2),
+    (3, (6, 7, 9), "vacuum", "window", "bf16", 2),
+    (9, (5, 4, 7), "periodic", "window", "fp32", 2),
+    (15, (4, 5, 9), "vacuum", "window", "fp32", 2),
+    (15, (3, 4, 6), "periodic", "window", "bf16", 2),
     (15, (7, 9, 40), "periodic", "stage", "fp32", 3),
     (15, (3, 5, 8), "vacuum", "stage", "bf16", 3),
     (39, (4, 5, 40), "vacuum", "auto", "fp32", 3),
@@ -87,11 +93,17 @@ def test_adjoint_non_cubic_vs_oracle(cuda_device, coupling_cache, precision, ker
 
 
 def test_non_cubic_rejections(cuda_device):
-    with rtpn.Context(7, (3, 4, 32), 0.1, "periodic", "fp32", 0.03) as ctx:
+    with rtpn.Context(39, (3, 4, 8), 0.1, "periodic", "fp32", 0.03) as ctx:
         ctx.set_kernel("window")
         with pytest.raises(rtpn.RtpnError) as e:
             ctx.set_spacing(*H3)
         assert e.value.code == rtpn.EUNSUPPORTED and ctx.info().hy == 0.1
+        ctx.set_kernel("auto")
+        ctx.set_spacing(*H3)
+        with pytest.raises(rtpn.RtpnError) as e:
+            ctx.set_kernel("window")
+        assert e.value.code == rtpn.EUNSUPPORTED
+    with rtpn.Context(7, (3, 4, 32), 0.1, "periodic", "fp32", 0.03) as ctx:
         ctx.set_kernel("fused")
         with pytest.raises(rtpn.RtpnError) as e:
             ctx.set_spacing(*H3)
@@ -102,8 +114,10 @@ def test_non_cubic_rejections(cuda_device):
         assert e.value.code == rtpn.ECFL and ctx.info().hy == 0.1
         ctx.set_spacing(*H3)
         with pytest.raises(rtpn.RtpnError) as e:
-            ctx.set_kernel("window")
+            ctx.set_kernel("fused")
         assert e.value.code == rtpn.EUNSUPPORTED
+        ctx.set_kernel("window")
+        assert ctx.info().kernel == 2
     insts = synth.batch_instances(2, seed=3)
     b = rtpn.Batch([(i.N, i.shape, i.h, i.bc, i.dt) for i in insts], "fp32")
     try:
