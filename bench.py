@@ -368,12 +368,13 @@ def main():
     if not args.no_e2e:
         e2e = end_to_end(ctx, inst, args, mcu_step, world, dist)
 
+    # the host baseline and the form measurements are one-GPU figures: rank 0 of a one-rank run
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, steps=5)
 
     forms = None
-    if rank == 0 and not args.no_forms and args.precision == "fp32":
+    if rank == 0 and world == 1 and not args.no_forms and args.precision == "fp32":
         forms = measure_forms(args, ctx, stream, step_ms, mcu_step)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
