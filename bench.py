@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true",
                    help="skip the BF16 / batched / adjoint form measurements")
-    p.add_argument("--forms", default="bf16,fused,reactor,batched,adjoint",
+    p.add_argument("--forms", default="bf16,fused,reactor,batched,adjoint,scattering",
                    help="which form measurements to run (comma-separated)")
     p.add_argument("--record-traffic", default=None,
                    help="write profiles/stage_traffic.json from an ncu CSV of this workload, then exit")
@@ -604,6 +604,33 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
                                    max(abs(res["window_u0_sum"]), 1e-300),
                 "value": 64 * V / (res["fused"] / 1e3) / 1e6, "unit": UNIT}
 
+    def scattering():
+        # anisotropic scattering (Henyey-Greenstein moments f_l = g^l, g = 0.8) at P7 128^3 FP32:
+        # the window kernel's anisotropic form against the generic kernel and the isotropic step
+        inst = synth.random_blocks(7, 128, seed=2)
+        f = [0.8 ** l for l in range(8)]
+        res = {}
+        for name, kernel, aniso in (("window_isotropic", "window", False), ("window", "window", True),
+                                    ("generic", "generic", True)):
+            with rtpn.Context(7, inst.shape, inst.h, inst.bc, "fp32", inst.dt) as c:
+                c.set_stream(stream)
+                c.set_kernel(kernel)
+                if aniso:
+                    c.set_scattering(f)
+                c.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+                c.set_component(0, inst.u0)
+                c.step(3)
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                c.step(50)
+                e.record(stream)
+                torch.cuda.synchronize()
+                res[name] = a.elapsed_time(e) / 50
+        return {"workload": "P7 128^3 random-block media, periodic, FP32, 50 steps, f_l = 0.8^l",
+                "ms_per_step": res, "window_vs_isotropic": res["window"] / res["window_isotropic"],
+                "speedup_vs_generic": res["generic"] / res["window"],
+                "note": "error bound 1e-5 (FP32) against the oracle checked in the GPU tests"}
+
     def reactor():
         # the reactor-like showcase (Section 5.2) as a P_N convergence study against P39
         from paper_2004_02833_gb300 import showcase
@@ -614,7 +641,7 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
 
     wanted = set(args.forms.split(","))
     for name, fn in (("bf16", bf16), ("fused", fused), ("reactor", reactor), ("batched", batched),
-                     ("adjoint", adjoint)):
+                     ("adjoint", adjoint), ("scattering", scattering)):
         if name in wanted:
             out[name] = _guard(fn)
     return out

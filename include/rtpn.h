@@ -131,9 +131,11 @@ int rtpn_destroy(rtpn_ctx* ctx);
  * Sigma_sl = f[l] * sigma_s with f[0] = 1 (sigma_s is Sigma_s0) and -1 <= f[l] <= 1, count = N + 1
  * (e.g. f[l] = g^l for a Henyey-Greenstein phase function); f = NULL or count = 0 restores isotropic
  * scattering.  Components of order l then decay by sigma_a + (1 - f[l]) sigma_s (mean over the
- * cells adjacent to their sub-grid point, as for isotropic media).  Runs on the generic kernel only:
+ * cells adjacent to their sub-grid point, as for isotropic media).  Runs on the generic kernel and,
+ * for N <= 15 in FP32/BF16, on the window kernel (each target reads its own order's factor planes):
  * RTPN_EUNSUPPORTED if another kernel is selected explicitly, for a batch instance, and later for
- * rtpn_adjoint; RTPN_KERNEL_AUTO moves to the generic kernel.  Allocates 32 (N + 1) more factor
+ * rtpn_adjoint; RTPN_KERNEL_AUTO moves to the window kernel where it applies, else to the generic
+ * one.  Allocates 32 (N + 1) more factor
  * planes (RTPN_ENOMEM leaves the context unchanged) and recomputes the factors of the media already
  * set; synchronises the context stream.  RTPN_EINVAL on a bad count or f. */
 int rtpn_set_scattering(rtpn_ctx* ctx, const double* f, int count);

@@ -138,7 +138,8 @@ int run_pass(rtpn_ctx* ctx, int cls, int fac_ofs, cudaStream_t st) {
         w.fac = (const float*)ctx->fac;
         w.g = ctx->g;
         w.cls = cls;
-        w.fac_ofs = fac_ofs;
+        w.aniso = ctx->scat != nullptr;
+        w.fac_ofs = w.aniso && fac_ofs == FAC_HALF ? aniso_half_ofs(ctx->N) : fac_ofs;
         const bool own_tile = ctx->active_kernel == RTPN_KERNEL_WINDOW;
         w.tx = own_tile ? ctx->tx : 0;
         w.ty = own_tile ? ctx->ty : 0;
@@ -355,14 +356,17 @@ int choose_kernel(rtpn_ctx* ctx) {
     int k = ctx->kernel;
     const bool cubic = cubic_cells(ctx->g);
     if (ctx->scat) {
-        // per-order factors are read through the generic kernel's per-target plane table only
-        if (k != RTPN_KERNEL_AUTO && k != RTPN_KERNEL_GENERIC)
-            return fail(ctx, RTPN_EUNSUPPORTED, "anisotropic scattering runs on the generic kernel only");
-        k = RTPN_KERNEL_GENERIC;
+        // per-order factors: the generic kernel's per-target plane table, or the window kernel's
+        // anisotropic form (N <= 15), which reads each target's planes at its finish
+        const bool win_aniso = window_supported(ctx->N, ctx->prec) && window_extended(ctx->N);
+        if (k == RTPN_KERNEL_AUTO) k = win_aniso ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
+        if (k != RTPN_KERNEL_GENERIC && !(k == RTPN_KERNEL_WINDOW && win_aniso))
+            return fail(ctx, RTPN_EUNSUPPORTED,
+                        "anisotropic scattering runs on the generic kernel and the window kernel up to N = 15");
     }
     // the window kernel takes non-cubic cells up to N = 15 (scaled y and z differences); the fused
     // kernel takes cubic cells only
-    const bool win_ok = window_supported(ctx->N, ctx->prec) && (cubic || window_takes_non_cubic(ctx->N));
+    const bool win_ok = window_supported(ctx->N, ctx->prec) && (cubic || window_extended(ctx->N));
     if (k == RTPN_KERNEL_AUTO) {
         const bool tile_set = ctx->tx || ctx->ty || ctx->tz;
         if (kStageInAuto && (ctx->N >= kStageMinN || !win_ok) &&
@@ -372,9 +376,16 @@ int choose_kernel(rtpn_ctx* ctx) {
         else
             k = win_ok ? RTPN_KERNEL_WINDOW : RTPN_KERNEL_GENERIC;
     }
+    // a tile the staged kernel chose is no request for another kernel (its shape need not even be a
+    // valid window tile): the other kernels start from their defaults
+    if (k != RTPN_KERNEL_STAGE && ctx->tile_from_stage) {
+        ctx->tx = ctx->ty = ctx->tz = 0;
+        ctx->depth = 0;
+        ctx->tile_from_stage = false;
+    }
     if (!cubic && k == RTPN_KERNEL_FUSED)
         return fail(ctx, RTPN_EUNSUPPORTED, "the fused kernel takes cubic cells only");
-    if (!cubic && k == RTPN_KERNEL_WINDOW && !window_takes_non_cubic(ctx->N))
+    if (!cubic && k == RTPN_KERNEL_WINDOW && !window_extended(ctx->N))
         return fail(ctx, RTPN_EUNSUPPORTED, "the window kernel takes non-cubic cells up to N = 15 only");
     if (k == RTPN_KERNEL_STAGE) {
         if (!stage_supported(ctx->N, ctx->prec, ctx->g.nx))
@@ -561,7 +572,7 @@ int rtpn_set_spacing(rtpn_ctx* ctx, double hx, double hy, double hz) {
         return fail(ctx, code, msg);
     };
     if (!cubic && (ctx->kernel == RTPN_KERNEL_FUSED ||
-                   (ctx->kernel == RTPN_KERNEL_WINDOW && !window_takes_non_cubic(ctx->N))))
+                   (ctx->kernel == RTPN_KERNEL_WINDOW && !window_extended(ctx->N))))
         return restore(RTPN_EUNSUPPORTED, "the fused kernel, and the window kernel above N = 15, take cubic cells only");
     // the partner tables and the staged kernel's constants carry the spacing: rebuild them
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -585,8 +596,11 @@ int rtpn_set_scattering(rtpn_ctx* ctx, const double* f, int count) {
             if (!(f[l] >= -1.0 && f[l] <= 1.0)) return fail(ctx, RTPN_EINVAL, "f_l must lie in [-1, 1]");
         if (ctx->batch_member)
             return fail(ctx, RTPN_EUNSUPPORTED, "batch instances take isotropic scattering only");
-        if (ctx->kernel != RTPN_KERNEL_AUTO && ctx->kernel != RTPN_KERNEL_GENERIC)
-            return fail(ctx, RTPN_EUNSUPPORTED, "anisotropic scattering runs on the generic kernel only");
+        const bool win_aniso = window_supported(ctx->N, ctx->prec) && window_extended(ctx->N);
+        if (ctx->kernel != RTPN_KERNEL_AUTO && ctx->kernel != RTPN_KERNEL_GENERIC &&
+            !(ctx->kernel == RTPN_KERNEL_WINDOW && win_aniso))
+            return fail(ctx, RTPN_EUNSUPPORTED,
+                        "anisotropic scattering runs on the generic kernel and the window kernel up to N = 15");
     }
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     const long long V = ctx->g.V;
@@ -664,11 +678,13 @@ int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int ti
             return fail(ctx, RTPN_EINVAL, "tile must hold a multiple of 32 threads, at most 256");
     }
     const int old = ctx->kernel, ox = ctx->tx, oy = ctx->ty, oz = ctx->tz, oc = ctx->depth;
+    const bool ofs = ctx->tile_from_stage;
     ctx->kernel = kernel;
     drop_graphs(ctx);
     ctx->tx = tile_x;
     ctx->ty = tile_y;
     ctx->tz = tile_z;
+    ctx->tile_from_stage = false;
     ctx->depth = kernel == RTPN_KERNEL_STAGE || kernel == RTPN_KERNEL_AUTO ? depth : 0;
     int rc = choose_kernel(ctx);
     if (rc) {
@@ -678,6 +694,7 @@ int rtpn_set_kernel_ex(rtpn_ctx* ctx, int kernel, int tile_x, int tile_y, int ti
         ctx->ty = oy;
         ctx->tz = oz;
         ctx->depth = oc;
+        ctx->tile_from_stage = ofs;
         choose_kernel(ctx);
         ctx->err = msg;
     }

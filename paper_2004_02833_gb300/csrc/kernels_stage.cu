@@ -164,6 +164,7 @@ int stage_prepare(rtpn_ctx* ctx, int tx, int ty, int tz, int depth) {
     ctx->ty = v->ty;
     ctx->tz = v->tz;
     ctx->depth = v->depth;
+    ctx->tile_from_stage = true;
     return 0;
 }
 

@@ -45,7 +45,7 @@ bool window_supported(int N, int precision) {
     return precision != RTPN_FP64 && win::find(N) != nullptr;
 }
 
-bool window_takes_non_cubic(int N) { return N <= win::kScaledMaxN; }
+bool window_extended(int N) { return N <= win::kExtendedMaxN; }
 
 int window_prepare(const Model& md, double, int precision) {
     static std::mutex mu;
@@ -82,6 +82,7 @@ int launch_window(int N, int precision, const WindowLaunch& w, cudaStream_t st) 
     a.inv_h = (float)(1.0 / w.g.h);
     a.sy = (float)(w.g.h / w.g.hy);  // exactly 1 for cubic cells
     a.sz = (float)(w.g.h / w.g.hz);
+    a.aniso = w.aniso ? 1 : 0;
     a.tx = w.tx > 0 ? w.tx : 32;
     a.ty = w.ty > 0 ? w.ty : 4;
     a.tz = w.tz > 0 ? w.tz : 2;

@@ -24,8 +24,8 @@ constexpr int FAC_U0 = 32;     // u_0 (c = sigma_a), tau = dt: alpha, beta, beta
 constexpr int FAC_PLANES = 35;
 // Anisotropic scattering (generic kernel only): after the 35 planes above, alpha and beta of every
 // (slot code g, order l) at tau = dt, then the same at tau = dt/2 (offset aniso_half_ofs(N)).
-__host__ __device__ inline int aniso_plane(int N, int g, int l) { return FAC_PLANES + 2 * (g * (N + 1) + l); }
-__host__ __device__ inline int aniso_half_ofs(int N) { return 16 * (N + 1); }
+__host__ __device__ constexpr int aniso_plane(int N, int g, int l) { return FAC_PLANES + 2 * (g * (N + 1) + l); }
+__host__ __device__ constexpr int aniso_half_ofs(int N) { return 16 * (N + 1); }
 __host__ __device__ inline int aniso_planes(int N) { return FAC_PLANES + 32 * (N + 1); }
 
 struct Geom {
@@ -82,12 +82,13 @@ struct WindowLaunch {
     const float* fac;       // factor planes
     Geom g;
     int cls;                // target class
-    int fac_ofs;            // FAC_FULL or FAC_HALF
+    int fac_ofs;            // FAC_FULL or FAC_HALF (anisotropic: 0 or aniso_half_ofs(N))
     int tx, ty, tz;         // CTA tile
+    bool aniso = false;     // per-order factor planes (anisotropic scattering)
 };
 // returns false if (N, precision) is not compiled in
 bool window_supported(int N, int precision);
-bool window_takes_non_cubic(int N);  // the window kernel's scaled form is compiled for this N
+bool window_extended(int N);  // the window kernel's non-cubic and anisotropic forms are compiled for N
 // uploads the coefficient constants of order N (idempotent); returns cudaError_t
 int window_prepare(const Model& md, double h, int precision);
 int launch_window(int N, int precision, const WindowLaunch& w, cudaStream_t st);
@@ -174,6 +175,7 @@ struct rtpn_ctx {
     void* stage_mem = nullptr;       // staged kernels: coupling tables of both classes + column starts
     size_t stage_tab_bytes[2] = {0, 0};
     int stage_variant = -1, sms = 0;
+    bool tile_from_stage = false;    // tx, ty, tz, depth describe the staged variant in use (not a request)
     void* stage_maps_dev = nullptr;  // CUtensorMap of the staged kernel (device global memory): those over
                                      // u, then the adjoint's (over its w, then over its lam)
     const void* stage_adj_lam = nullptr;  // arrays the adjoint maps were built for

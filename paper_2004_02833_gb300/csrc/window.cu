@@ -26,11 +26,39 @@ static_assert(kSources * 10 * 4 <= 64 * 1024 - 1024, "coefficient table exceeds 
 // coefficient of source j (class 1 - kA, local index) for relation k: M_d[a][b] * dir
 __constant__ float c_coef[kSources * 10];
 
-template <typename S, bool SCALED>
+template <typename S, bool SCALED, bool ANISO>
 __global__ void __launch_bounds__(256) k_window(Args a) {
     int x, y, z;
     if (!cell_of(a, blockIdx.x, threadIdx.x, &x, &y, &z)) return;
-    substep_cell<kN, kA, S, SCALED>(a, c_coef, x, y, z);
+    substep_cell<kN, kA, S, SCALED, ANISO>(a, c_coef, x, y, z);
+}
+
+template <bool SCALED, bool ANISO>
+int launch_form(int precision, const Args& a, cudaStream_t st) {
+    const int threads = a.tx * a.ty * a.tz;
+    const unsigned blocks = (unsigned)a.ntx * a.nty * a.ntz;
+    if (precision == RTPN_BF16)
+        k_window<__nv_bfloat16, SCALED, ANISO><<<blocks, threads, 0, st>>>(a);
+    else
+        k_window<float, SCALED, ANISO><<<blocks, threads, 0, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+// the form a launch needs; the non-cubic and anisotropic forms exist up to kExtendedMaxN (a
+// template, so that the discarded branch is not instantiated for larger orders)
+template <int NN>
+int launch_any(int precision, const Args& a, cudaStream_t st) {
+    const bool scaled = a.sy != 1.f || a.sz != 1.f;
+    if (scaled || a.aniso) {
+        if constexpr (NN <= kExtendedMaxN) {
+            if (scaled && a.aniso) return launch_form<true, true>(precision, a, st);
+            if (scaled) return launch_form<true, false>(precision, a, st);
+            return launch_form<false, true>(precision, a, st);
+        } else {
+            return (int)cudaErrorNotSupported;
+        }
+    }
+    return launch_form<false, false>(precision, a, st);
 }
 
 }  // namespace
@@ -41,23 +69,7 @@ int RTPN_VARIANT(window_upload)(const float* host, int count) {
 }
 
 int RTPN_VARIANT(window_launch)(int precision, const Args& a, cudaStream_t st) {
-    const int threads = a.tx * a.ty * a.tz;
-    const unsigned blocks = (unsigned)a.ntx * a.nty * a.ntz;
-    if (a.sy != 1.f || a.sz != 1.f) {
-        if constexpr (kN <= kScaledMaxN) {
-            if (precision == RTPN_BF16)
-                k_window<__nv_bfloat16, true><<<blocks, threads, 0, st>>>(a);
-            else
-                k_window<float, true><<<blocks, threads, 0, st>>>(a);
-            return (int)cudaGetLastError();
-        }
-        return (int)cudaErrorNotSupported;
-    }
-    if (precision == RTPN_BF16)
-        k_window<__nv_bfloat16, false><<<blocks, threads, 0, st>>>(a);
-    else
-        k_window<float, false><<<blocks, threads, 0, st>>>(a);
-    return (int)cudaGetLastError();
+    return launch_any<kN>(precision, a, st);
 }
 
 }  // namespace win

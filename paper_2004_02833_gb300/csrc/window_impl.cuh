@@ -158,6 +158,7 @@ struct Args {
     int tx, ty, tz;     // CTA tile (threads = tx*ty*tz)
     int ntx, nty, ntz;  // tiles per axis
     float sy = 1.f, sz = 1.f;  // h / h_y, h / h_z: the y and z differences' scale (non-cubic cells)
+    int aniso = 0;             // factors per (sub-grid, order l): anisotropic scattering
 };
 
 // coef[j * 10 + k]: source j (local index in class B), relation k: M_d[a][b] * dir, where dir = +1 if
@@ -177,10 +178,13 @@ RTPN_HD bool cell_of(const Args& a, int blk, int tid, int* x, int* y, int* z) {
 
 // SCALED: non-cubic cells (Section 2.1 divides each difference by its own axis' cell size); the
 // y and z differences are scaled by h / h_y and h / h_z, and 1/h (of x) is applied per target.
-// Compiled up to order kScaledMaxN: P39 runs non-cubic cells on the staged kernel, and its window
-// body is the slowest to compile.
-constexpr int kScaledMaxN = 15;
-template <int N, int A, typename S, bool SCALED = false>
+// ANISO: anisotropic scattering (Section 2, Sigma_tl = Sigma_a + Sigma_s0 - Sigma_sl): every target
+// (l, M, t) reads the factors of its own (sub-grid, order l) planes at finish instead of the four
+// per-sub-grid pairs (the same factor planes as the generic kernel; u_0 keeps its own).
+// Both forms are compiled up to order kExtendedMaxN: P39 runs non-cubic cells on the staged
+// kernel, and its window body is the slowest to compile.
+constexpr int kExtendedMaxN = 15;
+template <int N, int A, typename S, bool SCALED = false, bool ANISO = false>
 RTPN_HD void substep_cell(const Args& a, const float* __restrict__ coef, int x, int y, int z) {
     constexpr int B = 1 - A;
     constexpr int NL = N / 2 + 1;
@@ -216,7 +220,7 @@ RTPN_HD void substep_cell(const Args& a, const float* __restrict__ coef, int x, 
     static_for<8>([&](auto gi) {
         constexpr int g = decltype(gi)::value;
         constexpr int twos = (g & 1) + ((g >> 1) & 1) + ((g >> 2) & 1);
-        if constexpr (twos % 2 == A) {
+        if constexpr (twos % 2 == A && !ANISO) {
             al[g] = ro(a.fac + (long long)(a.fac_ofs + 2 * g) * V + cell);
             be[g] = ro(a.fac + (long long)(a.fac_ofs + 2 * g + 1) * V + cell) * a.inv_h;
         }
@@ -254,6 +258,11 @@ RTPN_HD void substep_cell(const Args& a, const float* __restrict__ coef, int x, 
                         float nv;
                         if constexpr (A == 0 && l == 0) {
                             nv = fmaf(al0, old, fmaf(-be0, r, ga0));
+                        } else if constexpr (ANISO) {
+                            constexpr int pl = aniso_plane(N, slot_code(l, M, t), l);
+                            const float alv = ro(a.fac + (long long)(a.fac_ofs + pl) * V + cell);
+                            const float bev = ro(a.fac + (long long)(a.fac_ofs + pl + 1) * V + cell) * a.inv_h;
+                            nv = fmaf(alv, old, -bev * r);
                         } else {
                             constexpr int g = slot_code(l, M, t);
                             nv = fmaf(al[g], old, -be[g] * r);

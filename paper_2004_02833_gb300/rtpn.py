@@ -211,7 +211,7 @@ class Context:
     # -- configuration
     def set_scattering(self, f=None):
         """Anisotropic scattering moments f_l = Sigma_sl / sigma_s, l = 0..N (f_0 = 1); None restores
-        isotropic scattering (generic kernel only)."""
+        isotropic scattering.  Runs on the generic kernel, and on the window kernel up to N = 15."""
         if f is None:
             self._chk(lib().rtpn_set_scattering(self._p, None, 0))
             return
