@@ -447,6 +447,8 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
         big = np.abs(ref) > 1e-3 * np.abs(ref).max()
         l2 = {p: float(np.linalg.norm(res[p] - ref) / np.linalg.norm(ref)) for p in ("fp32", "bf16")}
         pw = {p: float((np.abs(res[p] - ref)[big] / np.abs(ref)[big]).max()) for p in ("fp32", "bf16")}
+        # and over u_0 alone (interface component 0)
+        u0e = {p: float(np.abs(res[p][0] - ref[0]).max() / np.abs(ref[0]).max()) for p in ("fp32", "bf16")}
         # the typical size of BF16 storage rounding after 100 steps (201 passes, unit roundoff
         # 2^-8, a random walk); the GPU tests check BF16 against the oracle's rounding model
         estimate = (2 * 100 + 1) ** 0.5 * 2.0 ** -8
@@ -455,6 +457,7 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
                 "pass_ms": per_pass, "pass_frac_of_copy_bw": pass_frac,
                 "max_rel_err_vs_fp64_100_steps_24cubed": err["bf16"], "rounding_estimate": estimate,
                 "rel_l2_err_vs_fp64": l2["bf16"], "pointwise_rel_err_vs_fp64": pw["bf16"],
+                "u0_max_rel_err_vs_fp64": u0e["bf16"], "fp32_u0_max_rel_err_vs_fp64": u0e["fp32"],
                 "fp32_max_rel_err_vs_fp64_100_steps_24cubed": err["fp32"], "fp32_bound": 1e-5,
                 "fp32_rel_l2_err_vs_fp64": l2["fp32"], "fp32_pointwise_rel_err_vs_fp64": pw["fp32"],
                 "pointwise_support": "cells and moments with |u_fp64| > 1e-3 max |u_fp64|"}
