@@ -609,26 +609,34 @@ def measure_forms(args, ctx32, stream, fp32_ms, mcu_step):
 
     def scattering():
         # anisotropic scattering (Henyey-Greenstein moments f_l = g^l, g = 0.8) at P7 128^3 FP32:
-        # the window kernel's anisotropic form against the generic kernel and the isotropic step
+        # the window kernel's anisotropic form against the generic kernel and the isotropic step;
+        # the three are timed in turn, twice, and each keeps its faster round
         inst = synth.random_blocks(7, 128, seed=2)
         f = [0.8 ** l for l in range(8)]
-        res = {}
+        ctxs = {}
         for name, kernel, aniso in (("window_isotropic", "window", False), ("window", "window", True),
                                     ("generic", "generic", True)):
-            with rtpn.Context(7, inst.shape, inst.h, inst.bc, "fp32", inst.dt) as c:
-                c.set_stream(stream)
-                c.set_kernel(kernel)
-                if aniso:
-                    c.set_scattering(f)
-                c.set_media(inst.sigma_a, inst.sigma_s, inst.q)
-                c.set_component(0, inst.u0)
-                c.step(3)
+            c = rtpn.Context(7, inst.shape, inst.h, inst.bc, "fp32", inst.dt)
+            c.set_stream(stream)
+            c.set_kernel(kernel)
+            if aniso:
+                c.set_scattering(f)
+            c.set_media(inst.sigma_a, inst.sigma_s, inst.q)
+            c.set_component(0, inst.u0)
+            c.step(3)
+            ctxs[name] = c
+        res = {}
+        for _ in range(2):
+            for name, c in ctxs.items():
                 a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 c.step(50)
                 e.record(stream)
                 torch.cuda.synchronize()
-                res[name] = a.elapsed_time(e) / 50
+                ms = a.elapsed_time(e) / 50
+                res[name] = min(ms, res.get(name, ms))
+        for c in ctxs.values():
+            c.close()
         return {"workload": "P7 128^3 random-block media, periodic, FP32, 50 steps, f_l = 0.8^l",
                 "ms_per_step": res, "window_vs_isotropic": res["window"] / res["window_isotropic"],
                 "speedup_vs_generic": res["generic"] / res["window"],
