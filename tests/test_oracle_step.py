@@ -340,3 +340,49 @@ def test_dE_matches_extended_precision():
         X = mpmath.mpf(float(x))
         ref = mpmath.mpf(1) / 2 if X == 0 else (mpmath.exp(X) * (X - 1) + 1) / X**2
         assert abs((mpmath.mpf(float(g)) - ref) / ref) <= 2e-15, x
+
+
+# ----------------------------------------------------------------------------- merged schedule
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("bc", ["periodic", "vacuum"])
+def test_two_odd_half_steps_are_one_odd_full_step(bc, coupling_cache):
+    # With the even class frozen the residual r of the odd class does not change, and Eq. (5)
+    # composes exactly: exp(-c t/2)^2 = exp(-c t) and (t/2) E(-c t/2) (1 + exp(-c t/2)) = t E(-c t).
+    # Media with sigma near 0 and up to 10 cover both ends of E.
+    shape = (4, 5, 6)
+    sa, ss, q = synth.random_media(shape, 31, 0.0, 10.0)
+    sa[0, 0, :] = 0.0
+    ss[0, 0, :3] = 0.0
+    P = _problem(7, shape, sa, ss, q, 0.1, 0.03, bc, coupling_cache)
+    u = synth.random_state(7, shape, 32)
+    halves = P.substep(P.substep(u, 1, 0.5 * P.dt), 1, 0.5 * P.dt)
+    full = P.substep(u, 1, P.dt)
+    assert _rel(halves, full) <= 1e-13
+
+
+def _merged_segments(P, u, k, m):
+    # the library's merged form of k steps, in segments of at most m steps: odd half pass, then
+    # even and odd full passes, closing with an even full pass and an odd half pass per segment
+    s = 0
+    while s < k:
+        n = min(m, k - s)
+        u = P.substep(u, 1, 0.5 * P.dt)
+        for j in range(n):
+            u = P.substep(u, 0, P.dt)
+            u = P.substep(u, 1, P.dt if j < n - 1 else 0.5 * P.dt)
+        s += n
+    return u
+
+
+@pytest.mark.parametrize("k,m", [(5, 5), (7, 3), (4, 1)])
+def test_merged_schedule_equals_eq6(k, m, coupling_cache):
+    # Eq. (6) taken literally (three substeps per step) against its merged form, whole or cut into
+    # segments (the step kernels' schedule, and the staged adjoint's)
+    shape = (5, 4, 6)
+    sa, ss, q = synth.random_media(shape, 33, 0.0, 4.0)
+    P = _problem(5, shape, sa, ss, q, 0.1, 0.03, "vacuum", coupling_cache)
+    u = synth.random_state(5, shape, 34)
+    assert _rel(_merged_segments(P, u, k, m), P.run(u, k)) <= 1e-13
