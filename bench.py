@@ -693,30 +693,55 @@ def pass_durations(ctx, stream, reps: int):
 
 
 def end_to_end(ctx, inst, args, mcu_step, world, dist):
-    """One user job through the C ABI with pinned host buffers: upload media and u_0, zero the
-    other moments, advance K steps, read u_0 back.  Copies are inside the timed region."""
+    """One user job through the C ABI with pinned host buffers, every copy inside the timed region:
+    upload the media and u_0 and zero the other moments; then every step its passes and a read of
+    its metric (the FP64 sum of u_0 after the step's even pass, where u_0 has finished the step) to
+    the host; at the end u_0 to the host.  On one rank the same job is timed once more reading the
+    whole state back at the end (`full_state`; under torchrun every rank would pin a state of host
+    memory)."""
     import torch
 
     host = [torch.tensor(a, dtype=torch.float32).pin_memory()
             for a in (inst.sigma_a, inst.sigma_s, inst.q, inst.u0)]
-    out = torch.empty(inst.shape, dtype=torch.float32).pin_memory()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    ctx.set_media(host[0], host[1], host[2])
-    ctx.zero_moments()
-    ctx.set_component(0, host[3])
-    ctx.step(args.steps)
-    ctx.get_component(0, out)
-    ctx.synchronize()
-    dt = time.perf_counter() - t0
-    dt_ms, units = aggregate(dt * 1e3, float(mcu_step * args.steps), dist, device="cuda")
     h2d = sum(h.numel() * 4 for h in host)
-    d2h = out.numel() * 4
-    return {"value": units / (dt_ms / 1e3) / 1e6, "unit": UNIT,
-            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-            "job": f"set_media + zero + set u_0 from pinned host, {args.steps} steps, u_0 to host"}
+
+    def job(out, read):
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ctx.set_media(host[0], host[1], host[2])
+        ctx.zero_moments()
+        ctx.set_component(0, host[3])
+        # the merged schedule pass by pass, with the step's metric between its even and odd passes
+        ctx.substep(1, half=True)
+        metrics = []
+        for s in range(args.steps):
+            ctx.substep(0)
+            metrics.append(ctx.sum_u0())
+            ctx.substep(1, half=s == args.steps - 1)
+        read(out)
+        ctx.synchronize()
+        dt = time.perf_counter() - t0
+        dt_ms, units = aggregate(dt * 1e3, float(mcu_step * args.steps), dist, device="cuda")
+        d2h = 8 * args.steps + out.numel() * 4
+        return {"value": units / (dt_ms / 1e3) / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+
+    u0_out = torch.empty(inst.shape, dtype=torch.float32).pin_memory()
+    e2e = job(u0_out, lambda o: ctx.get_component(0, o))
+    e2e["job"] = (f"set_media + zero + set u_0 from pinned host, {args.steps} steps each with its sum "
+                  f"of u_0 read to the host, then u_0 to pinned host memory")
+    if world == 1:
+        try:
+            full = torch.empty((ctx.info().n_c,) + tuple(inst.shape), dtype=torch.float32, pin_memory=True)
+        except RuntimeError:
+            full = None
+        if full is not None:
+            e2e["full_state"] = job(full, lambda o: ctx.get_moments(o))
+            e2e["full_state"]["job"] = "the same job reading the whole state back at the end"
+            del full
+    return e2e
 
 
 if __name__ == "__main__":
