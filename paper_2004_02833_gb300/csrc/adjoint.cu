@@ -647,6 +647,7 @@ int adjoint_staged(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* 
         cudaMemcpyAsync(dst, X(sg, m), even_b, cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(dst + even_b, X(sg, m + 1) + even_b, odd_b, cudaMemcpyDeviceToDevice, st);
     }
+    ctx->steps_done += k;  // the context now holds u(k), whatever the backward sweep meets
     // J = sum w u_0 (u_0 is internal component 0)
     k_dot_u0<float><<<1024, 256, 0, st>>>((const float*)ctx->u, w_dev, V, (double*)part);
     launch_sum<double>((const double*)part, 1024, ctx->partial, 1, ctx->partial + SUM_BLOCKS, st);
@@ -687,7 +688,6 @@ int adjoint_staged(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return afail(ctx, RTPN_ECUDA, std::string("adjoint: ") + cudaGetErrorString(e));
     if (int rc = rtpn_synchronize(ctx)) return rc;  // also reports a staged wait that ran out
-    ctx->steps_done += k;
     return RTPN_OK;
 }
 
