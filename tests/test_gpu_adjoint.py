@@ -95,8 +95,10 @@ def test_adjoint_staged_segments_vs_oracle(cuda_device, coupling_cache, k, ckpt)
         assert ctx.info().kernel == 3
         ctx.set_media(inst.sigma_a, inst.sigma_s, inst.q)
         ctx.set_moments(u0)
+        before = ctx.info().steps_done
         J, (gsa, gss, gq) = ctx.adjoint(w, k, ckpt_every=ckpt)
         final = ctx.get_moments()
+        assert ctx.info().steps_done == before + k
     assert np.abs(inst.q).max() > 0
     assert abs(J - J_ref) <= 1e-4 * abs(J_ref)
     assert rel(gsa, gsa_ref) <= 1e-4 and rel(gss, gss_ref) <= 1e-4 and rel(gq, gq_ref) <= 1e-4
