@@ -36,7 +36,7 @@ struct Inst {
     const float* fac;
     long long V;
     long long block0;  // first work item of this instance
-    int nx, ny, nz, bc, N;
+    int nx, ny, nz, bc;
     float inv_h;
     int ntx, nty, ntz;
 };
@@ -202,7 +202,6 @@ int build_items(rtpn_batch* b) {
         I.ny = c->g.ny;
         I.nz = c->g.nz;
         I.bc = c->g.bc;
-        I.N = c->N;
         I.inv_h = (float)(1.0 / c->g.h);
         I.ntx = (I.nx + b->tx - 1) / b->tx;
         I.nty = (I.ny + b->ty - 1) / b->ty;
