@@ -499,7 +499,9 @@ __device__ __forceinline__ void stage_producer(const Args& a, unsigned char* buf
             static_for<NJOB>([&](auto jj) {
                 constexpr int j = decltype(jj)::value;
                 const BoxJob bj = stage_box<N, A, S, TX, TY, TZ, NB, EQ>(a, g, i, runs, offA_s, offB_s, j);
-                if (bj.valid && RTPN_SCHECK_ID(bj.c >= 0 && bj.c < a.nc && (bj.emap + 1) * EQ <= L::NL, 101, bj.c)) {
+                // sources: components of the source array (a.nc); targets: of a full state array (u or lam)
+                const int cmax = bj.target ? class_size(N, 0) + class_size(N, 1) : a.nc;
+                if (bj.valid && RTPN_SCHECK_ID(bj.c >= 0 && bj.c < cmax && (bj.emap + 1) * EQ <= L::NL, 101, bj.c)) {
                     const CUtensorMap* mp = bj.target ? a.tmap + bj.emap : maps + bj.kind * L::NMAP + bj.emap;
                     tma_load_4d(smem_addr(buf + bj.dst), mp, bj.x, bj.y, bj.z, bj.c, full);
                 }
