@@ -9,9 +9,13 @@
 //
 // Compile with -DRTPN_SN=<order> -DRTPN_STX= -DRTPN_STY= -DRTPN_STZ= -DRTPN_SNB= -DRTPN_SEM= (a
 // variant of stage_variants.h).
-// usage: emulate_stage cls nx ny nz bc h dt half fp32|bf16 sms in.bin out.bin
+// usage: emulate_stage cls nx ny nz bc h dt half fp32|bf16 sms in.bin out.bin [adjsrc|adjsrc_alpha]
 //   in.bin: float64 u [n_c][nz][ny][nx] (interface order), then sigma_a, sigma_s, q [nz][ny][nx]
 //   out.bin: float64 u after the substep of class cls (tau = dt, or dt/2 with half = 1)
+//   adjsrc: the adjoint's transposed coupling onto class cls instead (mode ADJ_SOURCES, FP32):
+//     in.bin holds lam [n_c] and w [n_c] (interface order; w of the other class is used), then
+//     the media; out.bin is lam after lam_B <- a lam_B + K w / h, with a = 1, or (adjsrc_alpha)
+//     the class's factor at tau (u_0: its own)
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -41,8 +45,11 @@ using namespace rtpn::stg;
 
 constexpr int kN = RTPN_SN, kTX = RTPN_STX, kTY = RTPN_STY, kTZ = RTPN_STZ, kNB = RTPN_SNB, kEQ = RTPN_SEM;
 
+// u: the target array (the state, or lam in mode ADJ_SOURCES), a full state; src: the source
+// array with src_nc components (the state itself, or w of the source class in its local order)
 template <int A, typename S>
-void run(Args a, const float* fac, S* u, const std::vector<float>& coef, int sms) {
+void run(Args a, const float* fac, S* u, const S* src, int src_nc, const std::vector<float>& coef, int sms,
+         int mode, bool use_alpha) {
     using L = Layout<kN, A, S, kTX, kTY, kTZ, kNB, kEQ>;
     constexpr int B = 1 - A, NST = kN + 2, NLA = (kN - A) / 2 + 1, CELLS = L::CELLS;
     constexpr int NJOB = 2 * L::NKIND + 2 * kTZ;
@@ -88,7 +95,8 @@ void run(Args a, const float* fac, S* u, const std::vector<float>& coef, int sms
                 if (bj.dst + bytes > region_end || region_end > L::COEFO) fail("box leaves its region", bj.dst);
                 if (((long long)bj.x * L::ES) % 16 != 0) fail("x coordinate not 16-byte aligned", bj.x);
                 if (E < 1 || E > L::NL) fail("box length", E);
-                const int nc = a.nc;  // sources and targets are both the state array here
+                const S* base = bj.target ? u : src;
+                const int nc = bj.target ? class_size(kN, 0) + class_size(kN, 1) : src_nc;
                 for (int ec = 0; ec < E; ++ec)
                     for (int ez = 0; ez < bz; ++ez)
                         for (int ey = 0; ey < by; ++ey)
@@ -96,7 +104,7 @@ void run(Args a, const float* fac, S* u, const std::vector<float>& coef, int sms
                                 const long long X = bj.x + ex, Y = bj.y + ey, Z = bj.z + ez, C = bj.c + ec;
                                 S v{};
                                 if (X >= 0 && X < a.nx && Y >= 0 && Y < a.ny && Z >= 0 && Z < a.nz && C >= 0 && C < nc) {
-                                    const S* p = u + C * V + (Z * a.ny + Y) * a.nx + X;
+                                    const S* p = base + C * V + (Z * a.ny + Y) * a.nx + X;
                                     check_ptr(p);
                                     v = *p;
                                 }
@@ -133,7 +141,8 @@ void run(Args a, const float* fac, S* u, const std::vector<float>& coef, int sms
                     const bool active = lx < g.wx && ly < g.wy && lz < g.wz;
                     const long long cell = ((long long)(g.z0 + lz) * a.ny + (g.y0 + ly)) * a.nx + (g.x0 + lx);
                     float alpha = 0.f, beta = 0.f, al0 = 0.f, be0 = 0.f, ga0 = 0.f;
-                    if (active) {
+                    if (mode == ADJ_SOURCES && !use_alpha) alpha = al0 = 1.f;
+                    if (active && (mode == FORWARD || use_alpha)) {
                         const int par = M & 1;
                         const int gx = ((par == 0) == (T == 0)) ? 0 : 1, gz = ((A + par) & 1) == 0 ? 0 : 1;
                         const int gc = gx + 2 * T + 4 * gz;
@@ -145,8 +154,12 @@ void run(Args a, const float* fac, S* u, const std::vector<float>& coef, int sms
                     }
                     const int tgo = L::TGTO + T * L::TGT_T + lz * L::REG + (ly * kTX + lx) * L::ES;
                     S* tp = u + (long long)(cA0 + offA + T * column_len(kN, M, A) - q0) * V + cell;
-                    finish_column<kN, A, S, kTX, kTY, kTZ, kNB, kEQ, FORWARD>(buf, tgo, M, T, tp, V, active, alpha,
-                                                                            beta, al0, be0, ga0, a.inv_h, prev);
+                    if (mode == FORWARD)
+                        finish_column<kN, A, S, kTX, kTY, kTZ, kNB, kEQ, FORWARD>(buf, tgo, M, T, tp, V, active, alpha,
+                                                                                beta, al0, be0, ga0, a.inv_h, prev);
+                    else
+                        finish_column<kN, A, S, kTX, kTY, kTZ, kNB, kEQ, ADJ_SOURCES>(
+                            buf, tgo, M, T, tp, V, active, alpha, beta, al0, be0, ga0, a.inv_h, prev);
                 }
                 std::fill(prev, prev + NLA, 0.f);
                 rot[tid] = (rot[tid] + 1) % 3;
@@ -169,17 +182,25 @@ int main(int argc, char** argv) {
     const int sms = atoi(argv[10]);
     const char* inf = argv[11];
     const char* outf = argv[12];
+    const std::string mode_s = argc > 13 ? argv[13] : "fwd";
+    const int mode = mode_s == "fwd" ? FORWARD : ADJ_SOURCES;
+    const bool use_alpha = mode_s == "adjsrc_alpha";
+    if (mode == ADJ_SOURCES && prec != "fp32") {
+        fprintf(stderr, "the transposed coupling runs on FP32 arrays\n");
+        return 2;
+    }
     const int N = kN;
     Model md = build_model(N);
     const long long V = (long long)nx * ny * nz;
-    std::vector<double> in((size_t)(md.nc + 3) * V);
+    const int narr = mode == FORWARD ? 1 : 2;  // u, or lam and w
+    std::vector<double> in((size_t)(narr * md.nc + 3) * V);
     FILE* f = fopen(inf, "rb");
     if (!f || fread(in.data(), 8, in.size(), f) != in.size()) {
         fprintf(stderr, "bad input\n");
         return 4;
     }
     fclose(f);
-    const double* sa = in.data() + (size_t)md.nc * V;
+    const double* sa = in.data() + (size_t)narr * md.nc * V;
     const double* ss = sa + V;
     const double* q = ss + V;
     // factor planes by the rule of rtpn_set_media (mean of sigma over the cells adjacent to a
@@ -246,6 +267,22 @@ int main(int argc, char** argv) {
     }
     a.src_c0 = A == 1 ? 0 : md.ne;  // the source class is the other one
     a.nc = md.nc;
+    // mode ADJ_SOURCES: w of the other class, in its local order, is the source array
+    const int aw0 = A == 1 ? 0 : md.ne, nw = A == 1 ? md.ne : md.no;
+    std::vector<float> wloc;
+    if (mode == ADJ_SOURCES) {
+        wloc.resize((size_t)nw * V);
+        const double* w = in.data() + (size_t)md.nc * V;
+        for (int c = 0; c < md.nc; ++c) {
+            const int ic = md.internal_of_abi[c];
+            if (ic < aw0 || ic >= aw0 + nw) continue;
+            for (long long i = 0; i < V; ++i) wloc[(size_t)(ic - aw0) * V + i] = (float)w[(size_t)c * V + i];
+        }
+        a.src_c0 = 0;
+        a.nc = nw;
+        g_lo[4] = (const char*)wloc.data();
+        g_hi[4] = (const char*)(wloc.data() + wloc.size());
+    }
     g_lo[0] = (const char*)fac.data();
     g_hi[0] = (const char*)(fac.data() + fac.size());
     g_lo[1] = (const char*)tab[A].data();
@@ -264,11 +301,19 @@ int main(int argc, char** argv) {
             }
         g_lo[2] = (const char*)u.data();
         g_hi[2] = (const char*)(u.data() + u.size());
-        g_nr = 4;
+        g_nr = mode == FORWARD ? 4 : 5;
+        const S* src = u.data();
+        int src_nc = md.nc;
+        if constexpr (sizeof(S) == 4) {
+            if (mode == ADJ_SOURCES) {
+                src = wloc.data();
+                src_nc = nw;
+            }
+        }
         if (A == 0)
-            run<0, S>(a, fac.data(), u.data(), tab[0], sms);
+            run<0, S>(a, fac.data(), u.data(), src, src_nc, tab[0], sms, mode, use_alpha);
         else
-            run<1, S>(a, fac.data(), u.data(), tab[1], sms);
+            run<1, S>(a, fac.data(), u.data(), src, src_nc, tab[1], sms, mode, use_alpha);
         for (int c = 0; c < md.nc; ++c)
             for (long long i = 0; i < V; ++i) {
                 const S v = u[(size_t)md.internal_of_abi[c] * V + i];
