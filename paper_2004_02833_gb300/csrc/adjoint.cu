@@ -26,6 +26,7 @@
 #include <string>
 #include <vector>
 
+#include "pull_impl.cuh"
 #include "rtpn_internal.h"
 
 namespace rtpn {
@@ -51,63 +52,13 @@ __device__ __forceinline__ bool nb_cell(const Geom& g, int x, int y, int z, int 
     return true;
 }
 
-// E'(x) for E(x) = expm1(x) / x of Eq. (5).  For |x| < 1 its Taylor polynomial
-// sum_{k<24} (k+1)/(k+2)! x^k by Horner's rule (coefficients built from the recurrence
-// c_k = c_{k-1} (k+1) / (k (k+2)), c_0 = 1/2; the tail is below 1e-23); for |x| >= 1 the form
-// (x e^x - expm1(x)) / x^2, whose numerator no longer cancels.  The closed form near 0 would lose
-// about eps / x^2 of its value (1e-10 at |x| = 1e-3).
-__device__ __forceinline__ double dE(double x) {
-    if (fabs(x) < 1.0) {
-        constexpr int K = 24;
-        double c[K];
-        c[0] = 0.5;
-#pragma unroll
-        for (int k = 1; k < K; ++k) c[k] = c[k - 1] * (double)(k + 1) / ((double)k * (double)(k + 2));
-        double p = c[K - 1];
-#pragma unroll
-        for (int k = K - 2; k >= 0; --k) p = fma(p, x, c[k]);
-        return p;
-    }
-    return (x * exp(x) - expm1(x)) / (x * x);
-}
-
-// dalpha/dc and dbeta/dc per slot code for tau = dt (planes 0..15) and dt/2 (16..31), u_0 (32, 33)
-constexpr int DFAC_PLANES = 34;
+using adj::DFAC_PLANES;
 
 template <typename F>
 __global__ void k_adj_factors(const double* __restrict__ sa, const double* __restrict__ ss, F* __restrict__ dfac,
                               Geom g, double dt) {
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= g.V) return;
-    const int x = (int)(cell % g.nx), y = (int)((cell / g.nx) % g.ny), z = (int)(cell / ((long long)g.nx * g.ny));
-    for (int code = 0; code < 8; ++code) {
-        const int gx = code & 1, gy = (code >> 1) & 1, gz = (code >> 2) & 1;
-        double sum = 0.0;
-        int cnt = 0;
-        for (int dz = 0; dz <= gz; ++dz)
-            for (int dy = 0; dy <= gy; ++dy)
-                for (int dx = 0; dx <= gx; ++dx) {
-                    int xx = x + dx, yy = y + dy, zz = z + dz;
-                    if (xx >= g.nx || yy >= g.ny || zz >= g.nz) {
-                        if (g.bc != RTPN_BC_PERIODIC) continue;
-                        if (xx >= g.nx) xx -= g.nx;
-                        if (yy >= g.ny) yy -= g.ny;
-                        if (zz >= g.nz) zz -= g.nz;
-                    }
-                    const long long j = ((long long)zz * g.ny + yy) * g.nx + xx;
-                    sum += sa[j] + ss[j];
-                    ++cnt;
-                }
-        const double c = sum / cnt;
-        for (int h = 0; h < 2; ++h) {
-            const double tau = h ? 0.5 * dt : dt;
-            dfac[(long long)(16 * h + 2 * code) * g.V + cell] = (F)(-tau * exp(-c * tau));
-            dfac[(long long)(16 * h + 2 * code + 1) * g.V + cell] = (F)(-tau * tau * dE(-c * tau));
-        }
-    }
-    const double c0 = sa[cell];
-    dfac[(long long)32 * g.V + cell] = (F)(-dt * exp(-c0 * dt));
-    dfac[(long long)33 * g.V + cell] = (F)(-dt * dt * dE(-c0 * dt));
+    if (cell < g.V) adj::factor_derivatives<F>(sa, ss, dfac, g, dt, cell);
 }
 
 // Targets of class A: forward residual on the pre-substep state, media gradients, w = beta lam,
@@ -192,20 +143,8 @@ __global__ void k_adj_sources(F* __restrict__ lam, const F* __restrict__ w, Part
     }
 }
 
-// The pull-back through a pass on class A between two stored FP32 states, cell by cell.  The pass
-// computed u_A' = alpha u_A + beta r_A (Eq. 5), so its residual is r_A = (u_A' - alpha u_A) / beta
-// (q included for u_0) and no stencil is needed: gacc[slot] += sum_a lam_a (dalpha u_a + dbeta r_a),
-// gq += beta_0 lam_0, w_a = beta_a lam_a.  lam_a <- alpha_a lam_a is left to the next transposed
-// coupling onto class A (the staged ADJ_SOURCES pass scales its targets), which saves a store.
-// Where two passes on class A follow each other (the odd half passes that close one checkpoint
-// segment and open the next), the later one's scaling is still pending when this one is pulled
-// back: pre_ofs >= 0 gives its factors, lam is scaled by them first and stored back.  upre, upost
-// and lam point at class A's first component; w holds class A in its local order.  grp: ngroups x {plane of alpha in
-// the factors (FAC_U0 for u_0), gacc slot, first, end} over idx, the local indices sharing those
-// factors.  One thread per 4 consecutive cells, as float4: V % 4 == 0 (the staged kernel's rows
-// are 16-byte multiples), so every plane starts 16-byte aligned.
-__device__ __forceinline__ float4 ld4_nc(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-
+// The pull-back through a pass on class A from its stored pre- and post-pass states, four cells per
+// thread (adj::pull_cells; V % 4 == 0, so every plane starts 16-byte aligned).
 __global__ void __launch_bounds__(256) k_adj_pull(const float* __restrict__ upre, const float* __restrict__ upost,
                                                   float* __restrict__ lam, float* __restrict__ w,
                                                   const float* __restrict__ fac, const float* __restrict__ dfac,
@@ -213,55 +152,8 @@ __global__ void __launch_bounds__(256) k_adj_pull(const float* __restrict__ upre
                                                   const int* __restrict__ idx, long long V,
                                                   double* __restrict__ gacc, double* __restrict__ gq) {
     const long long c0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    if (c0 >= V) return;
-    for (int gi = 0; gi < ngroups; ++gi) {
-        const int fp = __ldg(grp + 4 * gi), slot = __ldg(grp + 4 * gi + 1);
-        const int jb = __ldg(grp + 4 * gi + 2), je = __ldg(grp + 4 * gi + 3);
-        const bool u0 = fp == FAC_U0;
-        const long long ap = u0 ? FAC_U0 : fp + fac_ofs, dp = u0 ? 32 : fp + fac_ofs;
-        float al[4], be[4], da[4], db[4], ib[4], acc[4] = {0.f, 0.f, 0.f, 0.f}, gqa[4] = {0.f, 0.f, 0.f, 0.f};
-        float pre[4] = {1.f, 1.f, 1.f, 1.f};
-        if (pre_ofs >= 0) {
-            const float4 p4 = ld4_nc(fac + (u0 ? (long long)FAC_U0 : (long long)fp + pre_ofs) * V + c0);
-            pre[0] = p4.x, pre[1] = p4.y, pre[2] = p4.z, pre[3] = p4.w;
-        }
-        {
-            const float4 a4 = ld4_nc(fac + ap * V + c0), b4 = ld4_nc(fac + (ap + 1) * V + c0);
-            const float4 d4 = ld4_nc(dfac + dp * V + c0), e4 = ld4_nc(dfac + (dp + 1) * V + c0);
-            al[0] = a4.x, al[1] = a4.y, al[2] = a4.z, al[3] = a4.w;
-            be[0] = b4.x, be[1] = b4.y, be[2] = b4.z, be[3] = b4.w;
-            da[0] = d4.x, da[1] = d4.y, da[2] = d4.z, da[3] = d4.w;
-            db[0] = e4.x, db[1] = e4.y, db[2] = e4.z, db[3] = e4.w;
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) ib[c] = 1.f / be[c];
-#pragma unroll 2
-        for (int j = jb; j < je; ++j) {
-            const long long o = (long long)__ldg(idx + j) * V + c0;
-            const float4 u4 = ld4_nc(upre + o), p4 = ld4_nc(upost + o);
-            float4 l4 = *reinterpret_cast<const float4*>(lam + o);
-            if (pre_ofs >= 0) {
-                l4 = make_float4(pre[0] * l4.x, pre[1] * l4.y, pre[2] * l4.z, pre[3] * l4.w);
-                *reinterpret_cast<float4*>(lam + o) = l4;
-            }
-            const float u[4] = {u4.x, u4.y, u4.z, u4.w}, up[4] = {p4.x, p4.y, p4.z, p4.w};
-            const float la[4] = {l4.x, l4.y, l4.z, l4.w};
-            float wv[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float r = fmaf(-al[c], u[c], up[c]) * ib[c];
-                acc[c] = fmaf(la[c], fmaf(da[c], u[c], db[c] * r), acc[c]);
-                gqa[c] = fmaf(be[c], la[c], gqa[c]);
-                wv[c] = be[c] * la[c];
-            }
-            *reinterpret_cast<float4*>(w + o) = make_float4(wv[0], wv[1], wv[2], wv[3]);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            gacc[(long long)slot * V + c0 + c] += (double)acc[c];
-            if (u0) gq[c0 + c] += (double)gqa[c];
-        }
-    }
+    if (c0 < V)
+        adj::pull_cells(upre, upost, lam, w, fac, dfac, fac_ofs, pre_ofs, grp, ngroups, idx, V, c0, gacc, gq);
 }
 
 // Transpose of the point mean: every staggered point spreads its dJ/dc over its adjacent cells.
@@ -523,25 +415,8 @@ int adjoint_impl(rtpn_ctx* ctx, const double* w_dev, int k, int ckpt, double* gs
     return RTPN_OK;
 }
 
-// The class-cls components grouped by the factors they share, for k_adj_pull: {plane of alpha,
-// gacc slot, first, end} per group, then the local indices of every group.
-struct PullTable {
-    std::vector<int> grp, idx;
-};
-PullTable pull_table(const Model& md, int cls) {
-    const int a0 = cls == 0 ? 0 : md.ne, na = cls == 0 ? md.ne : md.no;
-    std::map<int, std::vector<int>> by_plane;
-    for (int t = 0; t < na; ++t) {
-        const int a = md.abi_of_internal[a0 + t];
-        by_plane[a == 0 ? FAC_U0 : 2 * slot_code(md.comp[a].slot)].push_back(t);
-    }
-    PullTable p;
-    for (const auto& [fp, ts] : by_plane) {
-        p.grp.insert(p.grp.end(), {fp, fp == FAC_U0 ? 8 : fp / 2, (int)p.idx.size(), (int)(p.idx.size() + ts.size())});
-        p.idx.insert(p.idx.end(), ts.begin(), ts.end());
-    }
-    return p;
-}
+using adj::PullTable;
+using adj::pull_table;
 
 // FP32 storage on the staged kernel.  The k steps run as segments of ckpt whole Strang steps, each in
 // the merged form of the step (odd half pass; even and odd full passes; even full pass; odd half
